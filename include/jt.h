@@ -1,0 +1,158 @@
+/*
+ * jt.h -- C ABI of libjt, a GB300 (sm_103a) library that applies the fast
+ * discrete Jacobi polynomial transform of Bremer, Pang and Yang, "Fast
+ * Algorithms for the Multi-dimensional Jacobi Polynomial Transform"
+ * (arXiv:1901.07275).
+ *
+ * Operators (per axis i, n_i points = n_i degrees, parameters a_i, b_i in (-1,1)):
+ *   uniform (Gauss--Jacobi nodes, Sec. 3.1 Eq. tf:transout):  A_i = W_i J_i,
+ *     (W_i J_i)[k][j] = sqrt(w_k) P~_j(t_k); A_i is orthogonal;
+ *   nonuniform (caller's angles t_k in (0,pi), Sec. 3.1 last paragraph): A_i = J_i,
+ *     J_i[k][j] = P~_j(t_k), with P~_j the modified Jacobi function of Eq.
+ *     eq:modifiedjac and degrees j = 0..n_i-1.
+ *   jt_forward :  f     = (A_0 (x) A_1 (x) ... ) alpha      (Eqs. eq:oneJ, eq:TJ, eq:TJ3)
+ *   jt_adjoint :  alpha = (A_0 (x) A_1 (x) ... )^T g        (Eqs. eq:oneJinv, eq:invTJ, eq:invTJ3)
+ *   jt_inverse :  the inverse of jt_forward; equals jt_adjoint for uniform axes
+ *                 (A_i orthogonal, Sec. 3.1); JT_ENOTSUP if any axis is nonuniform
+ *                 (the paper leaves that inverse open, Sec. 5).
+ *
+ * Each axis is applied as   A x = W V x_V + W Re( sum_k D_{u_k} F D_{v_k} x_G )   (Eq. eq:oneJ):
+ * V is the dense block of degrees < nu0 (27), F the row-gathered unnormalised
+ * inverse DFT of length L (Eqs. eq:lastJ, eq:permuDFT), u_k, v_k the rank-r factors
+ * of the matrix B (Eqs. eq:B, eq:approxA) built at plan creation by the randomised
+ * SVD of Algorithm 2.1.  d-dimensional transforms sweep the axes one at a time.
+ *
+ * Layout: arrays are row-major over (nrhs, n_0, ..., n_{d-1}); the last axis is
+ * contiguous and the right-hand-side index is slowest.  JT_FP32 plans take and
+ * return float32; JT_SPLIT and JT_FP64_PLAIN plans take and return float64.
+ *
+ * Memory: alpha, f and g are DEVICE pointers owned by the caller; calls are
+ * asynchronous on the given stream (NULL = legacy default stream) and never
+ * synchronise.  The plan owns its device tables; all entry points are
+ * thread-safe for distinct plans, and a plan is read-only after creation, so
+ * concurrent calls on one plan on different streams are safe as long as their
+ * output buffers do not overlap.  Input and output may be the same buffer
+ * (in-place transform).  No C++ exception crosses this interface.
+ */
+#ifndef JT_H
+#define JT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* jt_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    JT_OK = 0,
+    JT_EINVAL = 1,   /* invalid argument (sizes, parameters outside (-1,1), points outside (0,pi), ...) */
+    JT_ENOMEM = 2,   /* host or device allocation failed */
+    JT_ENOTSUP = 3,  /* operation not defined for this plan (nonuniform inverse, ...) */
+    JT_ECUDA = 4,    /* a CUDA runtime or library call failed */
+    JT_ETIMEOUT = 5, /* reserved: a bounded device wait expired */
+    JT_ENOCONV = 6   /* setup did not converge: rank needed for eps exceeds rank_cap, nodes not found */
+} jt_status;
+
+typedef enum {
+    JT_FP32 = 0,       /* fused FP32 axis kernels; float32 in/out */
+    JT_SPLIT = 1,      /* fused kernels in double-word (hi+lo FP32) arithmetic; float64 in/out */
+    JT_FP64_PLAIN = 2  /* unfused FP64 comparison path: the r^d d-dim FFT form (abstract,
+                          Sec. 5) with cuFFT Z2Z; float64 in/out */
+} jt_precision;
+
+typedef struct {
+    int32_t prec;           /* jt_precision */
+    int32_t nu0;            /* split degree of Eq. tf:jn; default 27 */
+    int32_t rank_cap;       /* largest rank allowed per axis; 0 => max(ceil(2 log2 n), 64) */
+    int32_t oversample_q;   /* oversampling factor q of Algorithm 2.1; default 3 */
+    uint64_t seed;          /* seed of the row/column sampling in Algorithm 2.1 */
+    int32_t fft_len_policy; /* 0: L = n if n is a power of two, else the next power of two */
+    int32_t autotune;       /* reserved, must be 0 */
+} jt_options;
+
+/* Fill *opt with the defaults listed above. */
+void jt_options_default(jt_options* opt);
+
+typedef struct jt_plan jt_plan;
+
+/*
+ * Create a plan for a d-dimensional transform (d in {1,2,3}).
+ *   n[i]      number of points (= number of degrees) on axis i, 1 <= n[i] <= 16384
+ *             (<= 8192 for JT_SPLIT)
+ *   a[i],b[i] Jacobi parameters, each in (-1, 1) (the method does not apply outside, Sec. 5)
+ *   points    NULL, or an array of d host pointers; points[i] == NULL selects the n[i]
+ *             Gauss--Jacobi nodes of axis i (uniform); otherwise points[i] holds n[i]
+ *             host float64 angles t in (0, pi) (nonuniform axis, W_i = I).
+ *   eps       relative accuracy of the low-rank factorisation, in (0, 1): singular values
+ *             below eps * sigma_1 are dropped (Sec. 2.1, rank-adaptive wrapper).
+ *   opt       NULL for defaults.
+ *   stream    stream for the table uploads; the call synchronises it before returning.
+ * Setup (nodes, phase data, factorisation) runs on the host in FP64; tables are then
+ * uploaded once.  Errors: JT_EINVAL, JT_ENOMEM, JT_ENOCONV, JT_ECUDA; *out is NULL on error.
+ */
+jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a, const double* b,
+                         const double* const* points, double eps, const jt_options* opt,
+                         jt_stream_t stream);
+
+/* Forward transform of nrhs >= 1 right-hand sides: f = (A_0 (x) ... ) alpha.  alpha and f
+ * hold nrhs * prod(n) elements of the plan's I/O type and may alias exactly. */
+jt_status jt_forward(jt_plan* plan, const void* alpha, void* f, int64_t nrhs, jt_stream_t stream);
+
+/* Adjoint (transpose): alpha = (A_0 (x) ... )^T g.  Same layout rules as jt_forward. */
+jt_status jt_adjoint(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt_stream_t stream);
+
+/* Inverse of jt_forward: equal to jt_adjoint when every axis is uniform; JT_ENOTSUP otherwise. */
+jt_status jt_inverse(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt_stream_t stream);
+
+/*
+ * Plan inspection.  For axis in [0, d): *rank = number of rank terms r, *fft_len = L.
+ * t_out / w_out (each NULL or n[axis] host float64): the points and the trigonometric
+ * Gauss--Jacobi weights w_k (1 for a nonuniform axis).  JT_EINVAL on a bad axis.
+ */
+jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_len, double* t_out,
+                       double* w_out);
+
+/* Release a plan and its device tables.  NULL is accepted. */
+void jt_destroy(jt_plan* plan);
+
+/* Static string naming a status code. */
+const char* jt_status_string(jt_status s);
+
+/* ------------------------------------------------------------------------------------
+ * Host-side setup of one axis, for inspection and testing of the plan tables.  Runs the
+ * same code as jt_plan_create for one axis and touches no GPU.
+ *   B-matrix factors (Eqs. eq:B, eq:approxA): the plan stores the row-scaled matrix
+ *   W B (W = diag(sqrt(w_k)) for a uniform axis, I otherwise) as sum_k u_k v_k^T with
+ *   u_k of length n and v_k of length n - nu0 (plain transpose, not conjugate).
+ * ------------------------------------------------------------------------------------ */
+typedef struct jt_axis_tables jt_axis_tables;
+
+jt_status jt_axis_tables_create(jt_axis_tables** out, int64_t n, double a, double b,
+                                const double* points, double eps, const jt_options* opt);
+
+/* Sizes: rank r, FFT length L, effective nu0 (= min(nu0, n)), and the sampled relative
+ * Frobenius error of sum_k u_k v_k^T against W B (any of the pointers may be NULL). */
+jt_status jt_axis_tables_info(const jt_axis_tables* t, int* rank, int64_t* fft_len, int* nu0,
+                              double* fact_err);
+
+/* Copy the tables to caller-owned host buffers (any may be NULL):
+ *   t[n] angles, w[n] trigonometric weights (1 if nonuniform), m[n] FFT bins round(t L / 2 pi),
+ *   u[2*r*n] interleaved (re,im) row-major r x n, v[2*r*(n-nu0)] interleaved r x (n-nu0),
+ *   vblk[n*nu0] row-major n x nu0 with vblk[k][c] = sqrt(w_k) P~_c(t_k). */
+jt_status jt_axis_tables_copy(const jt_axis_tables* t, double* tt, double* w, int32_t* m, double* u,
+                              double* v, double* vblk);
+
+/* Evaluate rows of the row-scaled matrix W B exactly (by recurrence), for testing:
+ * out[2*(i*(n-nu0)+c)+{0,1}] = (W B)[rows[i]][c]. */
+jt_status jt_axis_tables_b_rows(const jt_axis_tables* t, const int64_t* rows, int64_t nrows,
+                                double* out);
+
+void jt_axis_tables_destroy(jt_axis_tables* t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JT_H */

@@ -1,0 +1,269 @@
+// Plans and the transform entry points of the C ABI (include/jt.h).
+//
+// jt_plan_create runs the host setup of every axis (jt_setup.cpp), converts the tables to
+// the working precision, uploads them once, and keeps them for the lifetime of the plan.
+// jt_forward / jt_adjoint sweep the axes one at a time (Sec. 3.2--3.3, Eqs. eq:TJ, eq:TJ3,
+// eq:invTJ, eq:invTJ3): the first sweep reads the caller's input and writes the caller's
+// output, every later sweep works in place on the output, fibre by fibre, so no scratch
+// array is needed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "jt.h"
+#include "jt_internal.hpp"
+#include "jt_launch.hpp"
+#include "jt_plain.hpp"
+
+namespace {
+
+using jt::dev::AxisDev;
+using jt::dev::Cx;
+using jt::dev::dw;
+
+struct DeviceAxis {
+    jt::AxisTables host;
+    AxisDev dev{};
+    int log2L = 0;
+    std::vector<void*> allocs;
+};
+
+}  // namespace
+
+struct jt_plan {
+    int d = 0;
+    int prec = JT_FP32;
+    bool all_uniform = true;
+    int64_t n[3] = {1, 1, 1};
+    std::vector<DeviceAxis> axes;
+    jt::PlainPlan* plain = nullptr;  // JT_FP64_PLAIN resources
+};
+
+namespace {
+
+template <class T>
+jt_status upload(DeviceAxis& ax, const std::vector<T>& host, const void** dst, cudaStream_t s) {
+    if (host.empty()) {
+        *dst = nullptr;
+        return JT_OK;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * host.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return JT_ENOMEM;
+    }
+    ax.allocs.push_back(p);
+    if (cudaMemcpyAsync(p, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return JT_ECUDA;
+    *dst = p;
+    return JT_OK;
+}
+
+inline float to_r(double v, float*) { return (float)v; }
+inline dw to_r(double v, dw*) {
+    float h = (float)v;
+    return dw{h, (float)(v - (double)h)};
+}
+
+// Build and upload the device tables of one axis in precision R.
+template <class R>
+jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
+    const jt::AxisTables& T = ax.host;
+    const int64_t n = T.n, L = T.L, r = T.rank, nu0 = T.nu0, N = T.N;
+    R* tag = nullptr;
+    std::vector<Cx<R>> vtab((size_t)r * L, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
+    for (int64_t k = 0; k < r; ++k)
+        for (int64_t c = 0; c < N; ++c) {
+            const jt::cd v = T.V[(size_t)k * N + c];
+            vtab[(size_t)k * L + nu0 + c] = Cx<R>{to_r(v.real(), tag), to_r(v.imag(), tag)};
+        }
+    std::vector<Cx<R>> utab((size_t)r * n);
+    for (size_t i = 0; i < utab.size(); ++i) utab[i] = Cx<R>{to_r(T.U[i].real(), tag), to_r(T.U[i].imag(), tag)};
+    std::vector<R> vblk((size_t)nu0 * n);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t c = 0; c < nu0; ++c) vblk[(size_t)c * n + j] = to_r(T.Vblk[(size_t)j * nu0 + c], tag);
+    std::vector<Cx<R>> twid(L);
+    const double twopi = 6.283185307179586476925286766559;
+    for (int64_t q = 0; q < L; ++q) {
+        double ang = twopi * (double)q / (double)L;
+        twid[q] = Cx<R>{to_r(std::cos(ang), tag), to_r(std::sin(ang), tag)};
+    }
+    // bins: points of bin m are bin_idx[bin_ptr[m] .. bin_ptr[m+1]), m = 0..L/2
+    std::vector<int> bin_ptr(L / 2 + 2, 0), bin_idx(n);
+    for (int64_t j = 0; j < n; ++j) bin_ptr[T.m[j] + 1]++;
+    for (int64_t m = 0; m <= L / 2; ++m) bin_ptr[m + 1] += bin_ptr[m];
+    {
+        std::vector<int> fill(bin_ptr.begin(), bin_ptr.end() - 1);
+        for (int64_t j = 0; j < n; ++j) bin_idx[fill[T.m[j]]++] = (int)j;
+    }
+    std::vector<int> mtab(T.m.begin(), T.m.end());
+    AxisDev& A = ax.dev;
+    A.n = (int)n;
+    A.L = (int)L;
+    A.nu0 = (int)nu0;
+    A.rank = (int)r;
+    jt_status st;
+    const void* p;
+    if ((st = upload(ax, vtab, &A.vtab, s)) != JT_OK) return st;
+    if ((st = upload(ax, utab, &A.utab, s)) != JT_OK) return st;
+    if ((st = upload(ax, mtab, &p, s)) != JT_OK) return st;
+    A.mtab = (const int*)p;
+    if ((st = upload(ax, vblk, &A.vblk, s)) != JT_OK) return st;
+    if ((st = upload(ax, twid, &A.twid, s)) != JT_OK) return st;
+    if ((st = upload(ax, bin_ptr, &p, s)) != JT_OK) return st;
+    A.bin_ptr = (const int*)p;
+    if ((st = upload(ax, bin_idx, &p, s)) != JT_OK) return st;
+    A.bin_idx = (const int*)p;
+    // keep the host vectors alive until the copies are done
+    if (cudaStreamSynchronize(s) != cudaSuccess) return JT_ECUDA;
+    return JT_OK;
+}
+
+void free_axis(DeviceAxis& ax) {
+    for (void* p : ax.allocs) cudaFree(p);
+    ax.allocs.clear();
+}
+
+// Sweep every axis (last axis first).  Sweep 0 maps in -> out; later sweeps run in place.
+template <class IO>
+jt_status sweep(jt_plan* plan, const IO* in, IO* out, int64_t nrhs, bool fwd, cudaStream_t s) {
+    const int d = plan->d;
+    int64_t total = nrhs;
+    for (int i = 0; i < d; ++i) total *= plan->n[i];
+    const IO* src = in;
+    for (int ax = d - 1; ax >= 0; --ax) {
+        int64_t inner = 1;
+        for (int i = ax + 1; i < d; ++i) inner *= plan->n[i];
+        const int64_t nfib = total / plan->n[ax];
+        const DeviceAxis& A = plan->axes[ax];
+        cudaError_t e;
+        if constexpr (sizeof(IO) == 4)
+            e = jt::launch_axis_f32(A.dev, A.log2L, fwd, (const float*)src, (float*)out, nfib, inner, s);
+        else
+            e = jt::launch_axis_dw(A.dev, A.log2L, fwd, (const double*)src, (double*)out, nfib, inner, s);
+        if (e != cudaSuccess) return JT_ECUDA;
+        src = out;
+    }
+    return JT_OK;
+}
+
+jt_status apply(jt_plan* plan, const void* in, void* out, int64_t nrhs, bool fwd, cudaStream_t s) {
+    if (!plan || !in || !out || nrhs < 1) return JT_EINVAL;
+    int64_t total = nrhs;
+    for (int i = 0; i < plan->d; ++i) {
+        if (total > (int64_t(1) << 40) / plan->n[i]) return JT_EINVAL;
+        total *= plan->n[i];
+    }
+    try {
+        if (plan->prec == JT_FP32) return sweep<float>(plan, (const float*)in, (float*)out, nrhs, fwd, s);
+        if (plan->prec == JT_SPLIT) return sweep<double>(plan, (const double*)in, (double*)out, nrhs, fwd, s);
+        if (plan->prec == JT_FP64_PLAIN)
+            return jt::plain_apply(plan->plain, (const double*)in, (double*)out, nrhs, fwd, s);
+    } catch (...) {
+        return JT_ENOMEM;
+    }
+    return JT_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a, const double* b,
+                         const double* const* points, double eps, const jt_options* opt, jt_stream_t stream) {
+    if (!out) return JT_EINVAL;
+    *out = nullptr;
+    if (d < 1 || d > 3 || !n || !a || !b) return JT_EINVAL;
+    jt_options o;
+    jt_options_default(&o);
+    if (opt) o = *opt;
+    if (o.prec != JT_FP32 && o.prec != JT_SPLIT && o.prec != JT_FP64_PLAIN) return JT_EINVAL;
+    const int64_t nmax = (o.prec == JT_SPLIT) ? (int64_t(1) << jt::MAX_LOG2L_DW) : (int64_t(1) << jt::MAX_LOG2L_F32);
+    for (int i = 0; i < d; ++i) {
+        if (n[i] < 1 || !jt::valid_parameter(a[i]) || !jt::valid_parameter(b[i])) return JT_EINVAL;
+        if (n[i] > nmax) return JT_ENOTSUP;
+    }
+    if (!(eps > 0.0 && eps < 1.0)) return JT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    jt_plan* plan = nullptr;
+    try {
+        plan = new jt_plan();
+        plan->d = d;
+        plan->prec = o.prec;
+        plan->axes.resize(d);
+        for (int i = 0; i < d; ++i) {
+            plan->n[i] = n[i];
+            const double* pts = points ? points[i] : nullptr;
+            if (pts) plan->all_uniform = false;
+            jt_status st = jt::axis_setup(plan->axes[i].host, n[i], a[i], b[i], pts, eps, o);
+            if (st != JT_OK) {
+                jt_destroy(plan);
+                return st;
+            }
+            int lg = 0;
+            while ((int64_t(1) << lg) < plan->axes[i].host.L) ++lg;
+            plan->axes[i].log2L = lg;
+            if (o.prec == JT_FP32)
+                st = build_device_axis<float>(plan->axes[i], s);
+            else if (o.prec == JT_SPLIT)
+                st = build_device_axis<dw>(plan->axes[i], s);
+            if (st != JT_OK) {
+                jt_destroy(plan);
+                return st;
+            }
+        }
+        if (o.prec == JT_FP64_PLAIN) {
+            std::vector<const jt::AxisTables*> tabs;
+            for (auto& ax : plan->axes) tabs.push_back(&ax.host);
+            jt_status st = jt::plain_create(&plan->plain, tabs, s);
+            if (st != JT_OK) {
+                jt_destroy(plan);
+                return st;
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        jt_destroy(plan);
+        return JT_ENOMEM;
+    } catch (...) {
+        jt_destroy(plan);
+        return JT_EINVAL;
+    }
+    *out = plan;
+    return JT_OK;
+}
+
+jt_status jt_forward(jt_plan* plan, const void* alpha, void* f, int64_t nrhs, jt_stream_t stream) {
+    return apply(plan, alpha, f, nrhs, true, (cudaStream_t)stream);
+}
+
+jt_status jt_adjoint(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt_stream_t stream) {
+    return apply(plan, g, alpha, nrhs, false, (cudaStream_t)stream);
+}
+
+jt_status jt_inverse(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt_stream_t stream) {
+    if (!plan) return JT_EINVAL;
+    if (!plan->all_uniform) return JT_ENOTSUP;
+    return apply(plan, g, alpha, nrhs, false, (cudaStream_t)stream);
+}
+
+jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_len, double* t_out, double* w_out) {
+    if (!plan || axis < 0 || axis >= plan->d) return JT_EINVAL;
+    const jt::AxisTables& T = plan->axes[axis].host;
+    if (rank) *rank = T.rank;
+    if (fft_len) *fft_len = T.L;
+    if (t_out) std::memcpy(t_out, T.t.data(), sizeof(double) * T.n);
+    if (w_out) std::memcpy(w_out, T.w.data(), sizeof(double) * T.n);
+    return JT_OK;
+}
+
+void jt_destroy(jt_plan* plan) {
+    if (!plan) return;
+    for (auto& ax : plan->axes) free_axis(ax);
+    if (plan->plain) jt::plain_destroy(plan->plain);
+    delete plan;
+}
+
+}  // extern "C"

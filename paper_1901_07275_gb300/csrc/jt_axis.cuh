@@ -1,0 +1,496 @@
+// Fused axis kernels of the fast Jacobi transform (Sec. 3.1, Eqs. eq:oneJ and eq:oneJinv),
+// templated on the arithmetic: `float` (FP32) or `dw` (double-word: an unevaluated sum
+// hi + lo of two floats).
+//
+// One kernel launch applies the 1-D operator A = W [V, Re(sum_k D_{u_k} F D_{v_k})] (forward)
+// or its transpose (adjoint) to every fibre of one axis of a row-major array.  Per fibre,
+// a group of T threads keeps the fibre's data in registers and, for every rank term k,
+//   forward:  x = v_k .* alpha  (bins 0..L-1)  ->  y = IDFT_L(x)  ->  acc_j += Re(u_k[j] y[m_j])
+//   adjoint:  z[m] = sum_{j: m_j = m} u_k[j] g_j  ->  y = IDFT_L(z)  ->  acc_nu += Re(v_k[nu] y[nu])
+// with IDFT_L the unnormalised e^{+2 pi i m nu / L} transform, then adds the dense low-degree
+// block (degrees < nu0) and writes the fibre once.  The weights sqrt(w_j) are folded into
+// u_k and into the dense block at plan creation, so no separate scaling pass exists.
+//
+// FFT: Stockham auto-sort passes of radix <= 16.  Thread t of a group owns elements
+// t + T e (e < E = L / T) in registers; the first pass works entirely in registers, each
+// later pass exchanges through shared memory (padded one word per 32 against bank
+// conflicts), and the last pass leaves its outputs in the same t + T e layout.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace jt {
+namespace dev {
+
+// ------------------------------------------------------------ double-word floats
+// Dekker (1971) and Joldes, Muller, Popescu (ACM TOMS 2017): TwoSum, Fast2Sum, the
+// FMA-based exact product, AccurateDWPlusDW (relative error <= 3u^2) and DWTimesDW.
+struct dw {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dw two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dw operator+(dw x, dw y) {
+    dw s = two_sum(x.hi, y.hi);
+    dw t = two_sum(x.lo, y.lo);
+    dw v = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(v.hi, t.lo + v.lo);
+}
+__device__ __forceinline__ dw operator-(dw x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
+__device__ __forceinline__ dw operator*(dw x, dw y) {
+    float ch = x.hi * y.hi;
+    float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+    float tl0 = x.lo * y.lo;
+    float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+    float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+    return fast_two_sum(ch, cl1 + cl2);
+}
+
+template <class R>
+struct RealOps;
+template <>
+struct RealOps<float> {
+    using io = float;  // element type of the arrays the caller passes
+    static __host__ __device__ __forceinline__ float zero() { return 0.0f; }
+    static __device__ __forceinline__ float from_io(float v) { return v; }
+    static __device__ __forceinline__ float to_io(float v) { return v; }
+};
+template <>
+struct RealOps<dw> {
+    using io = double;
+    static __host__ __device__ __forceinline__ dw zero() { return {0.0f, 0.0f}; }
+    static __device__ __forceinline__ dw from_io(double v) {
+        float h = (float)v;
+        return {h, (float)(v - (double)h)};
+    }
+    static __device__ __forceinline__ double to_io(dw v) { return (double)v.hi + (double)v.lo; }
+};
+
+// compile-time constant in the working precision
+template <class R>
+__device__ __forceinline__ R rc(double v);
+template <>
+__device__ __forceinline__ float rc<float>(double v) {
+    return (float)v;
+}
+template <>
+__device__ __forceinline__ dw rc<dw>(double v) {
+    float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+template <class R>
+struct Cx {
+    R re, im;
+};
+template <class R>
+__device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) {
+    return {a.re + b.re, a.im + b.im};
+}
+template <class R>
+__device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) {
+    return {a.re - b.re, a.im - b.im};
+}
+template <class R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R>
+__device__ __forceinline__ Cx<R> mul_i(Cx<R> a) {  // multiply by +i
+    return {-a.im, a.re};
+}
+template <class R>
+__device__ __forceinline__ Cx<R> cscale(Cx<R> a, R s) {
+    return {a.re * s, a.im * s};
+}
+template <class R>
+__device__ __forceinline__ R re_mul(Cx<R> a, Cx<R> b) {  // Re(a b)
+    return a.re * b.re - a.im * b.im;
+}
+
+// Multiply by the twiddle e^{+2 pi i K / N} with compile-time K, N: the trivial cases
+// (1, i, -1, -i, (+-1 + i)/sqrt 2 ...) cost no general complex product.
+template <int K, int N, class R>
+__device__ __forceinline__ Cx<R> twc(Cx<R> v) {
+    constexpr int k = ((K % N) + N) % N;
+    if constexpr (k == 0) {
+        return v;
+    } else if constexpr (4 * k == N) {
+        return mul_i(v);
+    } else if constexpr (2 * k == N) {
+        return {-v.re, -v.im};
+    } else if constexpr (4 * k == 3 * N) {
+        return {v.im, -v.re};
+    } else if constexpr (8 * k == N || 8 * k == 3 * N || 8 * k == 5 * N || 8 * k == 7 * N) {
+        const R h = rc<R>(0.70710678118654752440084436210484903928);
+        // (1 + i)/sqrt2 rotated by the multiple of i
+        Cx<R> r{(v.re - v.im) * h, (v.re + v.im) * h};
+        if constexpr (8 * k == N) return r;
+        if constexpr (8 * k == 3 * N) return mul_i(r);
+        if constexpr (8 * k == 5 * N) return {-r.re, -r.im};
+        return {r.im, -r.re};
+    } else {
+        // remaining case: N = 16, k odd; e^{i pi k / 8} from cos(pi/8), sin(pi/8)
+        static_assert(N == 16 && (k & 1), "twiddle table covers radices up to 16");
+        constexpr double C8 = 0.92387953251128675612818318939678828682;
+        constexpr double S8 = 0.38268343236508977172845998403039886676;
+        constexpr double cr = (k == 1 || k == 15) ? C8 : (k == 3 || k == 13) ? S8 : (k == 5 || k == 11) ? -S8 : -C8;
+        constexpr double ci = (k == 1 || k == 7) ? S8 : (k == 3 || k == 5) ? C8 : (k == 9 || k == 15) ? -S8 : -C8;
+        const Cx<R> w{rc<R>(cr), rc<R>(ci)};
+        return cmul(v, w);
+    }
+}
+
+// Unnormalised DFT of size R with sign +: b_q = sum_r a_r e^{+2 pi i r q / R}, in natural
+// order, by radix-2 decimation in time with compile-time twiddles.
+template <int R>
+struct Bitrev {
+    static constexpr int lg = (R <= 1) ? 0 : (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
+    static constexpr __host__ __device__ int rev(int i) {
+        int r = 0;
+        for (int b = 0; b < lg; ++b)
+            if (i & (1 << b)) r |= 1 << (lg - 1 - b);
+        return r;
+    }
+};
+
+template <int LEN, int HALF, int K, class R>
+__device__ __forceinline__ void dft_stage_k(Cx<R>* t, int i) {
+    Cx<R> u = t[i + K];
+    Cx<R> v = twc<K, LEN, R>(t[i + K + HALF]);
+    t[i + K] = u + v;
+    t[i + K + HALF] = u - v;
+}
+
+template <int LEN, int R, class Rt>
+__device__ __forceinline__ void dft_stage(Cx<Rt>* t) {
+    constexpr int HALF = LEN / 2;
+#pragma unroll
+    for (int i = 0; i < R; i += LEN) {
+        if constexpr (HALF > 0) dft_stage_k<LEN, HALF, 0, Rt>(t, i);
+        if constexpr (HALF > 1) dft_stage_k<LEN, HALF, 1, Rt>(t, i);
+        if constexpr (HALF > 2) {
+            dft_stage_k<LEN, HALF, 2, Rt>(t, i);
+            dft_stage_k<LEN, HALF, 3, Rt>(t, i);
+        }
+        if constexpr (HALF > 4) {
+            dft_stage_k<LEN, HALF, 4, Rt>(t, i);
+            dft_stage_k<LEN, HALF, 5, Rt>(t, i);
+            dft_stage_k<LEN, HALF, 6, Rt>(t, i);
+            dft_stage_k<LEN, HALF, 7, Rt>(t, i);
+        }
+    }
+}
+
+template <int R, class Rt>
+__device__ __forceinline__ void dft(Cx<Rt>* a) {
+    if constexpr (R == 1) {
+        return;
+    } else {
+        Cx<Rt> t[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) t[Bitrev<R>::rev(i)] = a[i];
+        if constexpr (R >= 2) dft_stage<2, R, Rt>(t);
+        if constexpr (R >= 4) dft_stage<4, R, Rt>(t);
+        if constexpr (R >= 8) dft_stage<8, R, Rt>(t);
+        if constexpr (R >= 16) dft_stage<16, R, Rt>(t);
+#pragma unroll
+        for (int i = 0; i < R; ++i) a[i] = t[i];
+    }
+}
+
+// ------------------------------------------------------------------ geometry
+template <class R>
+struct RegRadix {
+    static constexpr int lg = 4;  // FP32: 16 complex elements per thread
+};
+template <>
+struct RegRadix<dw> {
+    static constexpr int lg = 3;  // double-word: 8 (twice the registers per element)
+};
+
+template <class R, int LOG2L>
+struct Shape {
+    static constexpr int LG = RegRadix<R>::lg;
+    static constexpr int EMAX = 1 << LG;
+    static constexpr int L = 1 << LOG2L;
+    static constexpr int E = (L < EMAX) ? L : EMAX;                      // elements per thread
+    static constexpr int T = L / E;                                      // threads per fibre
+    static constexpr int G = (T >= 256) ? 1 : 256 / T;                   // fibres per CTA
+    static constexpr int THREADS = G * T;
+    static constexpr int P = (LOG2L <= LG) ? 1 : (LOG2L + LG - 1) / LG;  // Stockham passes
+    static constexpr int R0 = 1 << (LOG2L - LG * (P - 1));               // radix of the first pass
+    static constexpr int PADL = L + (L >> 5) + 1;                     // padded complex buffer
+    static __host__ __device__ constexpr int pad(int i) { return i + (i >> 5); }
+};
+
+// Tables of one axis on the device (all owned by the plan).
+struct AxisDev {
+    int n, L, nu0, rank;
+    const void* vtab;    // rank x L   Cx<R>: v_k at bins nu0..n-1, zero elsewhere
+    const void* utab;    // rank x n   Cx<R>: sqrt(w_j) u_k[j]
+    const int* mtab;     // n          FFT bin of point j
+    const void* vblk;    // nu0 x n    R:     sqrt(w_j) P~_c(t_j)
+    const void* twid;    // L          Cx<R>: e^{+2 pi i s / L}
+    const int* bin_ptr;  // L/2 + 2    points of bin m: bin_idx[bin_ptr[m] .. bin_ptr[m+1])
+    const int* bin_idx;  // n
+};
+
+template <int T, int G>
+__device__ __forceinline__ void group_sync(int g) {
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else if constexpr (G == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(T) : "memory");
+    }
+}
+
+// One Stockham pass of radix RX over span NS (product of the earlier radices).  Inputs of
+// butterfly j = t + T b are x[b + r E/RX]; FIRST passes take them from registers, the others
+// from shared memory.  LAST passes leave outputs in registers at x[b + q E/RX] (element
+// t + T (b + q E/RX)); the others store them at their Stockham positions.
+template <class R, int LOG2L, int RX, int NS, bool FIRST, bool LAST>
+__device__ __forceinline__ void stockham_pass(Cx<R>* x, R* sre, R* sim, const Cx<R>* __restrict__ tw, int t,
+                                              int g) {
+    using S = Shape<R, LOG2L>;
+    constexpr int L = S::L, E = S::E, T = S::T, G = S::G;
+    constexpr int NB = E / RX;  // butterflies per thread
+    if constexpr (!FIRST) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            int b = e % NB, r = e / NB;
+            int idx = t + T * b + r * (L / RX);
+            x[e] = Cx<R>{sre[S::pad(idx)], sim[S::pad(idx)]};
+        }
+        group_sync<T, G>(g);  // every read done before this pass writes
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        Cx<R> a[RX];
+#pragma unroll
+        for (int r = 0; r < RX; ++r) a[r] = x[b + r * NB];
+        const int j = t + T * b;
+        const int k = j & (NS - 1);
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < RX; ++r) a[r] = cmul(a[r], tw[(r * k) * (L / (NS * RX))]);
+        }
+        dft<RX, R>(a);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int q = 0; q < RX; ++q) x[b + q * NB] = a[q];
+        } else {
+            const int base = (j - k) * RX + k;
+#pragma unroll
+            for (int q = 0; q < RX; ++q) {
+                int idx = base + q * NS;
+                sre[S::pad(idx)] = a[q].re;
+                sim[S::pad(idx)] = a[q].im;
+            }
+        }
+    }
+    if constexpr (!LAST) group_sync<T, G>(g);  // writes visible to the next pass
+}
+
+template <class R, int LOG2L, int PASS, int NS>
+__device__ __forceinline__ void fft_passes(Cx<R>* x, R* sre, R* sim, const Cx<R>* __restrict__ tw, int t, int g) {
+    using S = Shape<R, LOG2L>;
+    constexpr int RX = (PASS == 0) ? S::R0 : S::EMAX;
+    constexpr bool LAST = (PASS == S::P - 1);
+    stockham_pass<R, LOG2L, RX, NS, PASS == 0, LAST>(x, sre, sim, tw, t, g);
+    if constexpr (!LAST) fft_passes<R, LOG2L, PASS + 1, NS * RX>(x, sre, sim, tw, t, g);
+}
+
+// In-place unnormalised inverse DFT (sign +) of length L held in the t + T e layout.  The
+// caller guarantees that nobody still reads the shared buffer when this is entered.
+template <class R, int LOG2L>
+__device__ __forceinline__ void fft(Cx<R>* x, R* sre, R* sim, const Cx<R>* __restrict__ tw, int t, int g) {
+    fft_passes<R, LOG2L, 0, 1>(x, sre, sim, tw, t, g);
+}
+
+// ------------------------------------------------------------------ kernels
+template <class R, int LOG2L, bool FWD>
+__global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
+    axis_kernel(AxisDev A, const typename RealOps<R>::io* in, typename RealOps<R>::io* out, long long nfib,
+                long long inner) {
+    using S = Shape<R, LOG2L>;
+    using IO = typename RealOps<R>::io;
+    constexpr int L = S::L, E = S::E, T = S::T, G = S::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* smem = reinterpret_cast<R*>(smem_raw);
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x % T;
+    // per group: FFT buffer (re, im) then an auxiliary buffer of L reals
+    R* sre = smem + (size_t)g * (2 * S::PADL + L);
+    R* sim = sre + S::PADL;
+    R* aux = sim + S::PADL;
+
+    const int n = A.n, nu0 = A.nu0, rank = A.rank;
+    const Cx<R>* __restrict__ vtab = reinterpret_cast<const Cx<R>*>(A.vtab);
+    const Cx<R>* __restrict__ utab = reinterpret_cast<const Cx<R>*>(A.utab);
+    const R* __restrict__ vblk = reinterpret_cast<const R*>(A.vblk);
+    const Cx<R>* __restrict__ tw = reinterpret_cast<const Cx<R>*>(A.twid);
+    const long long ntiles = (nfib + G - 1) / G;
+
+    int mj[E];  // forward: bins of the owned output points
+    if constexpr (FWD) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            int j = t + T * e;
+            mj[e] = (j < n) ? __ldg(A.mtab + j) : 0;
+        }
+    }
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long f = tile * G + g;
+        const bool valid = f < nfib;
+        const long long o = valid ? f / inner : 0;
+        const long long q = valid ? f - o * inner : 0;
+        const long long base = o * (long long)n * inner + q;
+
+        R val[E];  // alpha (forward) or g (adjoint) at elements t + T e
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            int i = t + T * e;
+            val[e] = (valid && i < n) ? RealOps<R>::from_io(in[base + (long long)i * inner]) : RealOps<R>::zero();
+        }
+        R acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = RealOps<R>::zero();
+
+        if constexpr (FWD) {
+            // low-degree coefficients for the dense block, shared across the group
+            group_sync<T, G>(g);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                int i = t + T * e;
+                if (i < nu0) aux[i] = val[e];
+            }
+            group_sync<T, G>(g);
+            for (int k = 0; k < rank; ++k) {
+                Cx<R> x[E];
+                const Cx<R>* vk = vtab + (size_t)k * L;
+#pragma unroll
+                for (int e = 0; e < E; ++e) x[e] = cscale(vk[t + T * e], val[e]);
+                group_sync<T, G>(g);  // previous gather done with the buffer
+                fft<R, LOG2L>(x, sre, sim, tw, t, g);
+                group_sync<T, G>(g);  // last pass done reading the buffer
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int m = t + T * e;
+                    if (m <= L / 2) {
+                        sre[S::pad(m)] = x[e].re;
+                        sim[S::pad(m)] = x[e].im;
+                    }
+                }
+                group_sync<T, G>(g);
+                const Cx<R>* uk = utab + (size_t)k * n;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int j = t + T * e;
+                    if (j < n) {
+                        Cx<R> y{sre[S::pad(mj[e])], sim[S::pad(mj[e])]};
+                        acc[e] = acc[e] + re_mul(uk[j], y);
+                    }
+                }
+            }
+            // dense block: acc_j += sum_{c < nu0} sqrt(w_j) P~_c(t_j) alpha_c
+            for (int c = 0; c < nu0; ++c) {
+                R ac = aux[c];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int j = t + T * e;
+                    if (j < n) acc[e] = acc[e] + vblk[(size_t)c * n + j] * ac;
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int j = t + T * e;
+                    if (j < n) out[base + (long long)j * inner] = RealOps<R>::to_io(acc[e]);
+                }
+            }
+        } else {
+            // adjoint: g of the fibre in shared memory for the bin scatter
+            group_sync<T, G>(g);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                int j = t + T * e;
+                if (j < n) aux[j] = val[e];
+            }
+            group_sync<T, G>(g);
+            for (int k = 0; k < rank; ++k) {
+                const Cx<R>* uk = utab + (size_t)k * n;
+                Cx<R> x[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int m = t + T * e;
+                    Cx<R> z{RealOps<R>::zero(), RealOps<R>::zero()};
+                    if (m <= L / 2) {
+                        int p1 = __ldg(A.bin_ptr + m), p2 = __ldg(A.bin_ptr + m + 1);
+                        for (int p = p1; p < p2; ++p) {
+                            int j = __ldg(A.bin_idx + p);
+                            z = z + cscale(uk[j], aux[j]);
+                        }
+                    }
+                    x[e] = z;
+                }
+                group_sync<T, G>(g);  // previous FFT done with the buffer
+                fft<R, LOG2L>(x, sre, sim, tw, t, g);
+                const Cx<R>* vk = vtab + (size_t)k * L;
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[e] = acc[e] + re_mul(vk[t + T * e], x[e]);
+            }
+            // dense block: alpha_c = sum_j sqrt(w_j) P~_c(t_j) g_j for c < nu0; the group
+            // reduces its partial sums through the FFT buffer
+            for (int c = 0; c < nu0; ++c) {
+                R part = RealOps<R>::zero();
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int j = t + T * e;
+                    if (j < n) part = part + vblk[(size_t)c * n + j] * val[e];
+                }
+                group_sync<T, G>(g);
+                sre[t] = part;
+                group_sync<T, G>(g);
+                for (int s = T / 2; s > 0; s >>= 1) {
+                    if (t < s) sre[t] = sre[t] + sre[t + s];
+                    group_sync<T, G>(g);
+                }
+                R tot = sre[0];
+                // element c is owned by thread c % T at e = c / T
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (t + T * e == c) acc[e] = tot;
+            }
+            if (valid) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int j = t + T * e;
+                    if (j < n) out[base + (long long)j * inner] = RealOps<R>::to_io(acc[e]);
+                }
+            }
+        }
+    }
+}
+
+template <class R, int LOG2L>
+constexpr size_t axis_smem_bytes() {
+    using S = Shape<R, LOG2L>;
+    return sizeof(R) * (size_t)S::G * (2 * S::PADL + S::L);
+}
+
+}  // namespace dev
+}  // namespace jt

@@ -1,0 +1,20 @@
+// Launchers of the fused axis kernels, one translation unit per precision.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "jt_axis.cuh"
+
+namespace jt {
+
+// Apply one axis (forward or adjoint) to nfib fibres: fibre f = (o, q) with o = f / inner,
+// q = f % inner starts at o * n * inner + q and has stride inner.  in may equal out.
+cudaError_t launch_axis_f32(const dev::AxisDev& A, int log2L, bool fwd, const float* in, float* out,
+                            long long nfib, long long inner, cudaStream_t s);
+cudaError_t launch_axis_dw(const dev::AxisDev& A, int log2L, bool fwd, const double* in, double* out,
+                           long long nfib, long long inner, cudaStream_t s);
+
+constexpr int MAX_LOG2L_F32 = 14;
+constexpr int MAX_LOG2L_DW = 13;
+
+}  // namespace jt

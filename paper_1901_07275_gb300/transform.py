@@ -1,0 +1,141 @@
+"""PyTorch front end: device memory and streams come from torch, every step of the
+transform runs in libjt's kernels through the C ABI."""
+
+from __future__ import annotations
+
+import math
+
+from . import binding as B
+
+_DEFAULT_EPS = {"fp32": 1e-7, "split": 1e-12, "fp64_plain": 1e-12}
+_DTYPES = {"fp32": "float32", "split": "float64", "fp64_plain": "float64"}
+
+
+class Transform:
+    """A d-dimensional Jacobi transform plan (d = len(n)).
+
+    ``points[i]`` None selects the Gauss--Jacobi nodes of axis i (uniform, orthogonal
+    ``W J``); otherwise it holds the angles in (0, pi) of a nonuniform axis (``J``).
+    Inputs are torch tensors on the plan's CUDA device, contiguous, of shape
+    ``(..., n_0, .., n_{d-1})`` -- leading dimensions are independent right-hand sides --
+    and dtype float32 (``precision="fp32"``) or float64 (``"split"``, ``"fp64_plain"``).
+    """
+
+    def __init__(self, n, a, b, points=None, eps=None, precision="fp32", nu0=27, rank_cap=0,
+                 oversample_q=3, seed=None, stream=None):
+        import torch
+
+        self.n = tuple(int(v) for v in n)
+        self.d = len(self.n)
+        self.a = tuple(float(v) for v in a)
+        self.b = tuple(float(v) for v in b)
+        self.precision = precision
+        self.eps = _DEFAULT_EPS[precision] if eps is None else float(eps)
+        self.dtype = getattr(torch, _DTYPES[precision])
+        self.uniform = points is None or all(p is None for p in points)
+        opt = B.options(precision, nu0=nu0, rank_cap=rank_cap, oversample_q=oversample_q, seed=seed)
+        s = self._stream(stream)
+        self._plan = B.jt_plan_create(self.n, self.a, self.b, points, self.eps, opt, s)
+        self.info = [B.jt_plan_info(self._plan, i, self.n[i]) for i in range(self.d)]
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        return int(stream.cuda_stream)
+
+    @property
+    def ranks(self):
+        return [i["rank"] for i in self.info]
+
+    @property
+    def fft_lens(self):
+        return [i["fft_len"] for i in self.info]
+
+    def nodes(self, axis):
+        return self.info[axis]["t"]
+
+    def weights(self, axis):
+        return self.info[axis]["w"]
+
+    def _check(self, x):
+        import torch
+
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError("expected a CUDA tensor")
+        if x.dtype != self.dtype:
+            raise TypeError(f"expected dtype {self.dtype}, got {x.dtype}")
+        if tuple(x.shape[x.dim() - self.d:]) != self.n:
+            raise ValueError(f"trailing shape {tuple(x.shape)} does not match {self.n}")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        nrhs = math.prod(x.shape[: x.dim() - self.d]) if x.dim() > self.d else 1
+        return nrhs
+
+    def _run(self, fn, x, out, stream):
+        import torch
+
+        nrhs = self._check(x)
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            self._check(out)
+        if nrhs > 0:
+            fn(self._plan, x.data_ptr(), out.data_ptr(), nrhs, self._stream(stream))
+        return out
+
+    def forward(self, alpha, out=None, stream=None):
+        """f = (A_0 (x) .. (x) A_{d-1}) alpha."""
+        return self._run(B.jt_forward, alpha, out, stream)
+
+    def adjoint(self, g, out=None, stream=None):
+        """alpha = (A_0 (x) .. (x) A_{d-1})^T g."""
+        return self._run(B.jt_adjoint, g, out, stream)
+
+    def inverse(self, g, out=None, stream=None):
+        """Inverse of :meth:`forward` (uniform axes only)."""
+        return self._run(B.jt_inverse, g, out, stream)
+
+    __call__ = forward
+
+    def close(self):
+        if getattr(self, "_plan", None):
+            B.jt_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _make_fn():
+    import torch
+
+    class JacobiFn(torch.autograd.Function):
+        """f = T(alpha) with the hand-written adjoint kernel as its backward pass."""
+
+        @staticmethod
+        def forward(ctx, alpha, transform):
+            ctx.transform = transform
+            return transform.forward(alpha.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_f):
+            return ctx.transform.adjoint(grad_f.contiguous()), None
+
+    return JacobiFn
+
+
+_FN = None
+
+
+def jacobi_fn(alpha, transform):
+    """Differentiable forward transform (backward = adjoint kernel)."""
+    global _FN
+    if _FN is None:
+        _FN = _make_fn()
+    return _FN.apply(alpha, transform)

@@ -1,0 +1,89 @@
+"""The C-ABI library loads, exports every symbol ``include/jt.h`` declares, and rejects
+bad arguments on the host (no GPU needed for any of this)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1901_07275_gb300 import binding as B
+from paper_1901_07275_gb300 import build as build_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return B.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "jt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(jt_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(B.EXPORTS) == names
+
+
+def test_defaults_and_status_strings(lib):
+    o = B.Options()
+    lib.jt_options_default(ctypes.byref(o))
+    assert (o.prec, o.nu0, o.rank_cap, o.oversample_q, o.fft_len_policy, o.autotune) == (0, 27, 0, 3, 0, 0)
+    for s in range(7):
+        assert B.status_string(s).startswith("JT_")
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [
+        dict(n=[64], a=[1.0], b=[0.0]),
+        dict(n=[64], a=[0.0], b=[-1.0]),
+        dict(n=[64], a=[float("nan")], b=[0.0]),
+        dict(n=[0], a=[0.0], b=[0.0]),
+        dict(n=[64], a=[0.0], b=[0.0], eps=0.0),
+        dict(n=[64], a=[0.0], b=[0.0], eps=1.5),
+        dict(n=[8, 8, 8, 8], a=[0.0] * 4, b=[0.0] * 4),
+    ],
+)
+def test_plan_create_rejects_bad_arguments(lib, kw):
+    eps = kw.pop("eps", 1e-7)
+    with pytest.raises(B.JTError) as e:
+        B.jt_plan_create(kw["n"], kw["a"], kw["b"], None, eps)
+    assert e.value.status == B.JT_EINVAL
+
+
+def test_plan_create_rejects_points_outside_interval(lib):
+    with pytest.raises(B.JTError) as e:
+        B.jt_plan_create([4], [0.0], [0.0], [[0.1, 0.2, 3.2, 1.0]], 1e-7)
+    assert e.value.status == B.JT_EINVAL
+
+
+def test_too_long_axis_is_not_supported(lib):
+    with pytest.raises(B.JTError) as e:
+        B.jt_plan_create([16385], [0.0], [0.0], None, 1e-7)
+    assert e.value.status == B.JT_ENOTSUP
+    with pytest.raises(B.JTError) as e:
+        B.jt_plan_create([8193], [0.0], [0.0], None, 1e-12, B.options("split"))
+    assert e.value.status == B.JT_ENOTSUP
+
+
+def test_transform_calls_reject_null_plan(lib):
+    for fn in (lib.jt_forward, lib.jt_adjoint, lib.jt_inverse):
+        assert fn(None, None, None, 1, None) == B.JT_EINVAL
+    assert lib.jt_plan_info(None, 0, None, None, None, None) == B.JT_EINVAL
+    lib.jt_destroy(None)  # NULL-safe
+
+
+def test_axis_tables_reject_bad_arguments(lib):
+    for args in [(0, 0.0, 0.0), (10, -1.0, 0.0), (10, 0.0, 1.0)]:
+        with pytest.raises(B.JTError):
+            B.AxisTables(*args)

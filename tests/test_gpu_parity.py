@@ -1,0 +1,222 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (relative l2 over all outputs, or over the sampled outputs): 1e-5 for the
+FP32 kernels and 1e-10 for the double-word (split) kernels and the plain FP64 path, the
+accuracy targets of the method's GB300 build; factorisation accuracy eps = 1e-7 (FP32)
+and 1e-12 (split, plain).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_07275_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "split": 1e-10, "fp64_plain": 1e-10}
+EPS = {"fp32": 1e-7, "split": 1e-12, "fp64_plain": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return torch, torch.device("cuda:0")
+
+
+def rel(x, ref):
+    return np.linalg.norm(np.asarray(x, dtype=np.float64) - ref) / max(np.linalg.norm(ref), 1e-300)
+
+
+def make(n, ab, prec, points=None, eps=None):
+    from paper_1901_07275_gb300 import Transform
+
+    return Transform(n, [p[0] for p in ab], [p[1] for p in ab], points=points,
+                     eps=EPS[prec] if eps is None else eps, precision=prec)
+
+
+def to_dev(torch, dev, arr, prec):
+    return torch.tensor(arr, dtype=torch.float32 if prec == "fp32" else torch.float64, device=dev)
+
+
+def mats_for(n, ab, points=None):
+    pts = points or [None] * len(n)
+    return [oracle.axis_matrix(m, a, b, p) for m, (a, b), p in zip(n, ab, pts)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split"])
+@pytest.mark.parametrize("n", [1, 5, 27, 28, 33, 64, 100, 257, 512, 1000, 1024])
+def test_1d_forward_adjoint(torch_dev, prec, n):
+    torch, dev = torch_dev
+    ab = [(-0.25, 0.5)]
+    alpha = syn.normal(100 + n, 0, (3, n))
+    T = make((n,), ab, prec)
+    x = to_dev(torch, dev, alpha, prec)
+    f = T.forward(x)
+    g = T.adjoint(x)
+    M = mats_for((n,), ab)
+    assert rel(f.cpu().numpy(), oracle.forward(alpha, M)) < TOL[prec]
+    assert rel(g.cpu().numpy(), oracle.adjoint(alpha, M)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split", "fp64_plain"])
+def test_1d_1024_config(torch_dev, prec):
+    """n = 1024, (a, b) = (-0.25, 0.5), alpha ~ N(0, 1), eps = 1e-12 (1e-7 for FP32)."""
+    torch, dev = torch_dev
+    w = syn.workload("1d-1024", nrhs=4)
+    T = make(tuple(w["n"]), w["ab"], prec)
+    f = T.forward(to_dev(torch, dev, w["alpha"], prec))
+    M = mats_for(w["n"], w["ab"])
+    assert rel(f.cpu().numpy(), oracle.forward(w["alpha"], M)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split"])
+def test_2d_512_forward_and_inverse(torch_dev, prec):
+    """512 x 512, (0.3, -0.4) on axis 0 and (-0.5, 0.2) on axis 1: forward, and the inverse
+    applied to the oracle's forward output recovers alpha (Eqs. eq:TJ, eq:invTJ)."""
+    torch, dev = torch_dev
+    w = syn.workload("2d-512", nrhs=1)
+    T = make(tuple(w["n"]), w["ab"], prec)
+    M = mats_for(w["n"], w["ab"])
+    ref = oracle.forward(w["alpha"], M)
+    f = T.forward(to_dev(torch, dev, w["alpha"], prec))
+    assert rel(f.cpu().numpy(), ref) < TOL[prec]
+    back = T.inverse(to_dev(torch, dev, ref, prec))
+    assert rel(back.cpu().numpy(), w["alpha"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split"])
+def test_3d_small_forward_adjoint(torch_dev, prec):
+    torch, dev = torch_dev
+    n = (40, 33, 64)
+    ab = [(0.27, -0.45), (-0.16, 0.49), (-0.09, 0.13)]
+    alpha = syn.normal(33, 0, (2,) + n)
+    T = make(n, ab, prec)
+    M = mats_for(n, ab)
+    x = to_dev(torch, dev, alpha, prec)
+    assert rel(T.forward(x).cpu().numpy(), oracle.forward(alpha, M)) < TOL[prec]
+    assert rel(T.adjoint(x).cpu().numpy(), oracle.adjoint(alpha, M)) < TOL[prec]
+
+
+def test_3d_256_sampled(torch_dev):
+    """256^3, a_i, b_i ~ U(-0.5, 0.5), alpha ~ N(0,1)/(1+|nu|): 4096 seeded output entries."""
+    torch, dev = torch_dev
+    w = syn.workload("3d-256")
+    T = make(tuple(w["n"]), w["ab"], "fp32")
+    f = T.forward(to_dev(torch, dev, w["alpha"], "fp32")).cpu().numpy()[0]
+    idx = np.stack([syn.integers(w["seed"], 3, 4096, 0, 256) for _ in range(1)] * 1, axis=0)
+    idx = np.stack([syn.integers(w["seed"], 3 + 10 * a, 4096, 0, 256) for a in range(3)], axis=1)
+    rows = [oracle.uniform_rows(a, b, 256, idx[:, k]) for k, (a, b) in enumerate(w["ab"])]
+    ref = oracle.forward_sampled(w["alpha"][0], rows, idx)
+    assert rel(f[idx[:, 0], idx[:, 1], idx[:, 2]], ref) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split"])
+def test_2d_nonuniform_forward_adjoint(torch_dev, prec):
+    torch, dev = torch_dev
+    n = (128, 96)
+    ab = [(0.25, 0.25), (0.25, 0.25)]
+    pts = [np.sort(np.pi * syn.uniform(5, 2, (m,), offset=k * 1000)) for k, m in enumerate(n)]
+    alpha = syn.normal(5, 0, n)
+    T = make(n, ab, prec, points=pts)
+    M = mats_for(n, ab, pts)
+    x = to_dev(torch, dev, alpha, prec)
+    assert rel(T.forward(x).cpu().numpy(), oracle.forward(alpha, M)) < TOL[prec]
+    assert rel(T.adjoint(x).cpu().numpy(), oracle.adjoint(alpha, M)) < TOL[prec]
+    from paper_1901_07275_gb300 import binding as B
+
+    with pytest.raises(B.JTError) as e:
+        T.inverse(x)
+    assert e.value.status == B.JT_ENOTSUP
+
+
+@pytest.mark.parametrize("n", [(64, 48), (20, 24, 32), (300,)])
+def test_plain_fp64_path(torch_dev, n):
+    torch, dev = torch_dev
+    ab = [(0.3, -0.4), (-0.5, 0.2), (0.1, 0.1)][: len(n)]
+    alpha = syn.normal(77, 0, n)
+    T = make(n, ab, "fp64_plain")
+    M = mats_for(n, ab)
+    x = to_dev(torch, dev, alpha, "fp64_plain")
+    assert rel(T.forward(x).cpu().numpy(), oracle.forward(alpha, M)) < TOL["fp64_plain"]
+    assert rel(T.adjoint(x).cpu().numpy(), oracle.adjoint(alpha, M)) < TOL["fp64_plain"]
+
+
+def test_in_place_equals_out_of_place(torch_dev):
+    torch, dev = torch_dev
+    n = (96, 80)
+    ab = [(0.1, 0.2), (-0.3, 0.4)]
+    T = make(n, ab, "fp32")
+    x = to_dev(torch, dev, syn.normal(3, 0, (2,) + n), "fp32")
+    y = T.forward(x)
+    z = x.clone()
+    T.forward(z, out=z)
+    assert torch.equal(y, z)
+
+
+def test_repeated_runs_are_bitwise_identical(torch_dev):
+    torch, dev = torch_dev
+    n = (128, 64)
+    ab = [(0.1, 0.2), (-0.3, 0.4)]
+    for prec in ("fp32", "split"):
+        T = make(n, ab, prec)
+        x = to_dev(torch, dev, syn.normal(4, 0, n), prec)
+        assert torch.equal(T.forward(x), T.forward(x))
+        assert torch.equal(T.adjoint(x), T.adjoint(x))
+
+
+def test_nan_input_propagates_without_fault(torch_dev):
+    torch, dev = torch_dev
+    T = make((64,), [(0.0, 0.0)], "fp32")
+    x = to_dev(torch, dev, syn.normal(9, 0, (64,)), "fp32")
+    x[40] = float("nan")
+    f = T.forward(x)
+    torch.cuda.synchronize()
+    assert torch.isnan(f).any()
+
+
+def test_stability_round_trip(torch_dev):
+    """|| (WJ)^T (WJ) v - v || / || v || (Eq. eq:stability) at eps = 1e-8, 1-D n = 1024,
+    a = b = 0: of order 1e-8 (the paper prints 0.69e-8)."""
+    torch, dev = torch_dev
+    T = make((1024,), [(0.0, 0.0)], "split", eps=1e-8)
+    v = to_dev(torch, dev, syn.normal(12, 0, (4, 1024)), "split")
+    back = T.inverse(T.forward(v))
+    q = (back - v).norm(dim=1) / v.norm(dim=1)
+    assert float(q.max()) < 2e-7
+
+
+def test_autograd_gradient_matches_dense_transpose_and_finite_differences(torch_dev):
+    """Loss ||J alpha - y||^2 on a nonuniform 2-D grid (a = b = 0.25): the gradient through
+    the adjoint kernel equals 2 J^T (J alpha - y); central differences of a quadratic have
+    no truncation error, so a step of 1 isolates rounding."""
+    torch, dev = torch_dev
+    from paper_1901_07275_gb300 import jacobi_fn
+
+    n = (96, 64)
+    ab = [(0.25, 0.25), (0.25, 0.25)]
+    pts = [np.sort(np.pi * syn.uniform(1005, 2, (m,), offset=k * 100000)) for k, m in enumerate(n)]
+    alpha = syn.normal(1005, 0, n)
+    y = syn.normal(1005, 1, n)
+    T = make(n, ab, "fp32", points=pts)
+    a_t = to_dev(torch, dev, alpha, "fp32").requires_grad_(True)
+    y_t = to_dev(torch, dev, y, "fp32")
+    loss = ((jacobi_fn(a_t, T) - y_t) ** 2).sum()
+    loss.backward()
+    M = mats_for(n, ab, pts)
+    ref = 2 * oracle.adjoint(oracle.forward(alpha, M) - y, M)
+    grad = a_t.grad.double().cpu().numpy()
+    assert rel(grad, ref) < 1e-5
+    with torch.no_grad():
+        for k in range(8):
+            d = syn.normal(2000 + k, 0, n)
+            d /= np.linalg.norm(d)
+            dt = to_dev(torch, dev, d, "fp32")
+            lp = float(((jacobi_fn(a_t + dt, T) - y_t) ** 2).double().sum())
+            lm = float(((jacobi_fn(a_t - dt, T) - y_t) ** 2).double().sum())
+            fd = (lp - lm) / 2
+            assert abs(fd - float((grad * d).sum())) < 1e-4 * (abs(lp) + abs(lm))

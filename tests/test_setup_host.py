@@ -1,0 +1,136 @@
+"""Plan setup on the host (nodes, weights, bins, dense block and the low-rank factors of
+W B), checked against the CPU oracle and the paper's printed tables.  No GPU is used: the
+dense operator is rebuilt in numpy from the library's tables."""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_07275_gb300 import binding as B
+from paper_1901_07275_gb300 import build as build_mod
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build_mod.build()
+
+
+def dense_from_tables(T: B.AxisTables) -> np.ndarray:
+    """[W V, Re((sum_k u_k v_k^T) o F)] with F_{j,nu} = e^{2 pi i m_j nu / L} (Eq. eq:lastJ)."""
+    n, nu0 = T.n, T.nu0
+    G = T.U.T @ T.V
+    F = np.exp(2j * np.pi * np.outer(T.m, np.arange(nu0, n)) / T.L)
+    return np.concatenate([T.vblk, np.real(G * F)], axis=1)
+
+
+def read_golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            rows.append([float(v) for v in line.split()])
+    return rows
+
+
+@pytest.mark.parametrize(
+    "a,b,n,eps",
+    [
+        (-0.25, 0.5, 1024, 1e-12),
+        (0.3, -0.4, 512, 1e-7),
+        (-0.5, 0.2, 512, 1e-12),
+        (0.0, 0.0, 64, 1e-12),
+        (0.9, 0.9, 300, 1e-10),
+        (-0.9, -0.95, 256, 1e-12),
+        (0.25, 0.25, 28, 1e-12),
+        (0.25, 0.25, 30, 1e-12),
+        (0.1, 0.2, 27, 1e-12),
+        (0.1, 0.2, 5, 1e-12),
+        (0.1, 0.2, 1, 1e-12),
+    ],
+)
+def test_uniform_tables_rebuild_the_weighted_matrix(a, b, n, eps):
+    T = B.AxisTables(n, a, b, eps=eps)
+    Q = oracle.uniform_matrix(a, b, n)
+    t, _, _, w = oracle.gauss_jacobi(a, b, n)
+    assert np.abs(T.t - t.astype(float)).max() < 4 * np.finfo(float).eps * np.pi
+    assert np.abs(T.w / w.astype(float) - 1).max() < 1e-13
+    assert T.L >= n and (T.L & (T.L - 1)) == 0 and T.L < 2 * max(n, 1)
+    assert T.m.min() >= 0 and T.m.max() <= T.L // 2
+    D = dense_from_tables(T)
+    err = np.linalg.norm(D - Q) / np.linalg.norm(Q)
+    assert err < 20 * eps, err
+    assert T.fact_err < 20 * eps
+
+
+@pytest.mark.parametrize("a,b", [(0.25, 0.25), (-0.7, 0.6)])
+def test_nonuniform_tables_rebuild_J(a, b):
+    n = 300
+    rng = np.random.default_rng(5)
+    t = np.sort(rng.uniform(0, np.pi, n))
+    T = B.AxisTables(n, a, b, points=t, eps=1e-12)
+    J = oracle.nonuniform_matrix(t, a, b, n)
+    D = dense_from_tables(T)
+    assert np.allclose(T.w, 1.0)
+    assert np.linalg.norm(D - J) / np.linalg.norm(J) < 2e-11
+
+
+def test_real_part_of_B_times_F_is_the_high_degree_block_exactly():
+    """Eq. eq:lastJ: Re(B o F) equals the columns of degree >= nu0 of W J, whatever the
+    imaginary part (the second-kind function) is."""
+    a, b, n = 0.3, -0.4, 200
+    T = B.AxisTables(n, a, b, eps=1e-12)
+    rows = np.array([0, 1, 17, 99, 198, 199])
+    Bm = T.b_rows(rows)
+    F = np.exp(2j * np.pi * np.outer(T.m[rows], np.arange(T.nu0, n)) / T.L)
+    Q = oracle.uniform_matrix(a, b, n)[rows, T.nu0:]
+    assert np.abs(np.real(Bm * F) - Q).max() < 1e-13
+
+
+def test_B_is_non_oscillatory_in_the_chebyshev_case():
+    """a = b = -1/2: P~ + i Q~ = sqrt(2/pi) e^{i nu t}, so |B| = sqrt(w) sqrt(2/pi) on every row."""
+    n = 128
+    T = B.AxisTables(n, -0.5, -0.5, eps=1e-12)
+    Bm = T.b_rows(np.arange(n))
+    ref = np.sqrt(T.w)[:, None] * np.sqrt(2 / np.pi)
+    assert np.abs(np.abs(Bm) - ref).max() < 1e-12
+    assert T.rank <= 2
+
+
+@pytest.mark.parametrize("a_b,log2n,rank", [tuple(r) for r in read_golden("table1_ranks.txt")])
+def test_ranks_match_table_1(a_b, log2n, rank):
+    """RS ranks at eps = 1e-8 against Table 1.  The paper's rule for eps is not printed;
+    our spectral truncation is at most the paper's rank and within 3 of it."""
+    n = 2 ** int(log2n)
+    T = B.AxisTables(n, a_b, a_b, eps=1e-8)
+    assert rank - 3 <= T.rank <= rank
+
+
+@pytest.mark.parametrize("row", read_golden("stability_table.txt"))
+def test_stability_quantity_matches_table(row):
+    """|| A^T A v - v || / || v || of the fast operator at eps = 1e-8 is of order 1e-8
+    (within a factor 20 of the paper's value, or below 2e-9 where the paper's is tiny)."""
+    a_b, log2n, val = row
+    n = 2 ** int(log2n)
+    T = B.AxisTables(n, a_b, a_b, eps=1e-8)
+    A = dense_from_tables(T)
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for _ in range(4):
+        v = rng.standard_normal(n)
+        worst = max(worst, np.linalg.norm(A.T @ (A @ v) - v) / np.linalg.norm(v))
+    assert worst < max(20 * val * 1e-8, 2e-9), worst
+
+
+def test_factorisation_is_deterministic_and_seeded():
+    o1 = B.options(seed=1)
+    o2 = B.options(seed=2)
+    T1 = B.AxisTables(256, 0.1, -0.2, eps=1e-10, opt=o1)
+    T1b = B.AxisTables(256, 0.1, -0.2, eps=1e-10, opt=o1)
+    T2 = B.AxisTables(256, 0.1, -0.2, eps=1e-10, opt=o2)
+    assert np.array_equal(T1.U, T1b.U) and np.array_equal(T1.V, T1b.V)
+    D1, D2 = dense_from_tables(T1), dense_from_tables(T2)
+    assert np.linalg.norm(D1 - D2) / np.linalg.norm(D1) < 1e-9
