@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Throughput of the fast Jacobi transform on one GB300 (or N replicas).
+
+Workload: the 2-D uniform tensor-grid transform of size 512 x 512 with (a, b) = (0.3, -0.4)
+on axis 0 and (-0.5, 0.2) on axis 1, alpha i.i.d. N(0, 1) from the seeded generator,
+batched over ``--nrhs`` right-hand sides (default 256, i.e. 256 MiB of FP32 input -- larger
+than the 129 MB L2, so no L2 flush is needed between steps).  One step = one forward
+transform followed by one inverse transform of the whole batch with the fused FP32 axis
+kernels (factorisation accuracy 1e-7).  The metric is Jacobi coefficients per second:
+2 * nrhs * 512^2 per step.
+
+Also reported on the same line: the double-word (split) kernels, the plain FP64 r^2-FFT
+path (cuFFT Z2Z), accuracy against the CPU oracle, the end-to-end number through host
+buffers, the roofline of the axis kernel, and the oracle timed on the host cores.
+
+``--impl reference`` times the CPU oracle (dense mode products in FP64) on a bounded
+sample of the same workload and prints the same line with "impl": "reference".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = (512, 512)
+AB = [(0.3, -0.4), (-0.5, 0.2)]
+METRIC = "Jacobi coeffs/sec (2-D 512x512 forward+inverse, FP32 fused axis kernels, rel l2 <= 1e-5 vs FP64 oracle)"
+UNIT = "coeffs/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def axis_flops(n, L, r):
+    """Algorithmic FP32 flops of one fibre of one axis: r (5 L log2 L + 8 n) + 55 n."""
+    return r * (5 * L * math.log2(L) + 8 * n) + 55 * n
+
+
+def axis_table_bytes(n, L, r, nu0, real_bytes):
+    """Plan tables one launch reads once: v (r x L), u (r x n) complex, bins, dense block, twiddles."""
+    cplx = 2 * real_bytes
+    return r * L * cplx + r * n * cplx + 4 * n + nu0 * n * real_bytes + L * cplx + 4 * (L // 2 + 2) + 4 * n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu_index = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_throughput(nrhs_max, target_s=12.0, threads=None):
+    """Dense FP64 mode products of the oracle on a bounded sample of right-hand sides.
+    Matrices are built once (their cost is reported separately); returns coeffs/s."""
+    import numpy as np
+
+    import oracle
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    t0 = time.perf_counter()
+    mats = [oracle.uniform_matrix(a, b, m) for (a, b), m in zip(AB, N)]
+    setup_s = time.perf_counter() - t0
+    probe = syn.normal(1002, 0, (1,) + N)
+    t0 = time.perf_counter()
+    f = oracle.forward(probe, mats)
+    oracle.adjoint(f, mats)
+    per_rhs = max(time.perf_counter() - t0, 1e-4)
+    s = int(max(1, min(nrhs_max, target_s / per_rhs)))
+    alpha = syn.normal(1002, 0, (s,) + N)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:  # repeat the batch until about target_s of CPU work has been timed
+        f = oracle.forward(alpha, mats)
+        oracle.adjoint(f, mats)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s or reps >= 64:
+            break
+    coeffs = 2 * s * N[0] * N[1] * reps
+    return {"value": coeffs / dt, "unit": UNIT, "cores": threads or os.cpu_count(), "kind": "oracle",
+            "sample": f"{reps} x {s} right-hand sides of the 512x512 workload, forward + inverse by dense "
+                      f"FP64 mode products ({dt:.1f} s); axis matrices built once in {setup_s:.1f} s, not counted",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    steps, warm = args.steps, args.warmup
+    import numpy as np
+
+    import oracle
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    mats = [oracle.uniform_matrix(a, b, m) for (a, b), m in zip(AB, N)]
+    probe = syn.normal(1002, 0, (1,) + N)
+    t0 = time.perf_counter()
+    oracle.adjoint(oracle.forward(probe, mats), mats)
+    per_rhs = max(time.perf_counter() - t0, 1e-4)
+    # each step: a bounded sample so that warm-up + steps end within about two minutes
+    s = int(max(1, min(args.nrhs, 120.0 / ((steps + warm) * per_rhs))))
+    alpha = syn.normal(1002, 0, (s,) + N)
+    for _ in range(warm):
+        oracle.adjoint(oracle.forward(alpha, mats), mats)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.adjoint(oracle.forward(alpha, mats), mats)
+    dt = time.perf_counter() - t0
+    coeffs = 2 * s * N[0] * N[1] * steps
+    v = coeffs / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+        "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2d-512x512 uniform, (a,b)=(0.3,-0.4)x(-0.5,0.2)", "nrhs": s,
+                   "step": "forward + inverse", "l2": "host CPU run"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{s} right-hand sides per step, dense FP64 mode products"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--nrhs", type=int, default=256)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="time the FP32 step only (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.no_extras:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_1901_07275_gb300 import Transform
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    dev = torch.device("cuda", local)
+    peaks, peak_src = load_peaks()
+    nrhs = args.nrhs
+    T = Transform(N, [p[0] for p in AB], [p[1] for p in AB], eps=1e-7, precision="fp32")
+    ranks, Ls = T.ranks, T.fft_lens
+    alpha = syn.normal(1002 + rank, 0, (nrhs,) + N)
+    x = torch.tensor(alpha, dtype=torch.float32, device=dev)
+    f = torch.empty_like(x)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        T.forward(x, out=f)
+        T.inverse(f, out=y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = vis.split(",")[local] if vis else str(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(gpu_index) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            T.forward(x, out=f)
+            ev[i][1].record(stream)
+            T.inverse(f, out=y)
+            ev[i][2].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    total_ms = max_over_ranks(world, t_start.elapsed_time(t_end))
+    kern_ms = sum(a.elapsed_time(b) + b.elapsed_time(c) for a, b, c in ev)
+    clocks = clk.summary()
+
+    coeffs_per_step = 2 * nrhs * N[0] * N[1]
+    value = world * coeffs_per_step * args.steps / (total_ms * 1e-3)
+
+    # roofline of the fused axis kernel: 4 launches per step (2 axes x forward/inverse)
+    flops_step = 2 * sum(nrhs * (N[0] * N[1] // N[a]) * axis_flops(N[a], Ls[a], ranks[a]) for a in range(2))
+    bytes_step = 2 * sum(2 * 4 * nrhs * N[0] * N[1] + axis_table_bytes(N[a], Ls[a], ranks[a], 27, 4) for a in range(2))
+    achieved_tflops = flops_step * args.steps / (kern_ms * 1e-3) / 1e12
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    hbm_gbs = bytes_step * args.steps / (kern_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    launches = 4 * args.steps
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "2d-512x512 uniform, (a,b)=(0.3,-0.4)x(-0.5,0.2), alpha~N(0,1)",
+                   "nrhs": nrhs, "step": "forward + inverse, fused FP32 axis kernels, eps=1e-7",
+                   "ranks": ranks, "fft_len": Ls,
+                   "l2": f"inputs {4 * nrhs * N[0] * N[1] / 2**20:.0f} MiB > L2 129 MB, no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / alu_peak, "traffic": None,
+                     "peak_note": f"FP32 CUDA-core peak {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                  f"{sm_max:.0f} MHz (sm_max from MEASURED_PEAKS: {peak_src})",
+                     "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                             "peak_source": peak_src}},
+        "clocks": clocks, "gpu_launches": launches,
+    }
+
+    if rank == 0 and not args.no_extras:
+        import oracle
+
+        # accuracy on right-hand side 0 against the oracle (forward, and the inverse of it)
+        mats = [oracle.uniform_matrix(a, b, m) for (a, b), m in zip(AB, N)]
+        ref = oracle.forward(alpha[:1], mats)
+        err_f = float(np.linalg.norm(f[:1].double().cpu().numpy() - ref) / np.linalg.norm(ref))
+        err_i = float(np.linalg.norm(y[:1].double().cpu().numpy() - alpha[:1]) / np.linalg.norm(alpha[:1]))
+        line["rel_err"] = {"fp32_forward": err_f, "fp32_inverse_of_forward": err_i}
+
+        # end to end through the public API with host buffers (pinned), copies inside the region
+        xh = torch.tensor(alpha, dtype=torch.float32).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        ke = min(args.steps, 5)
+        for _ in range(2):
+            x.copy_(xh, non_blocking=True)
+            step()
+            yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            x.copy_(xh, non_blocking=True)
+            step()
+            yh.copy_(y, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / ke
+        line["e2e"] = {"value": coeffs_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": xh.numel() * 4, "d2h_bytes_per_step": yh.numel() * 4,
+                       "ms_per_step": e2e_ms}
+        del xh, yh
+
+        # double-word (split) kernels on a batch of 64 (134 MB of FP64 input)
+        n2 = min(nrhs, 64)
+        T2 = Transform(N, [p[0] for p in AB], [p[1] for p in AB], eps=1e-12, precision="split")
+        x2 = torch.tensor(alpha[:n2], dtype=torch.float64, device=dev)
+        f2 = torch.empty_like(x2)
+        y2 = torch.empty_like(x2)
+        for _ in range(3):
+            T2.forward(x2, out=f2)
+            T2.inverse(f2, out=y2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ks = 5
+        for _ in range(ks):
+            T2.forward(x2, out=f2)
+            T2.inverse(f2, out=y2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        split_ms = e0.elapsed_time(e1) / ks
+        ref2 = ref
+        err2 = float(np.linalg.norm(f2[:1].cpu().numpy() - ref2) / np.linalg.norm(ref2))
+        err2i = float(np.linalg.norm(y2[:1].cpu().numpy() - alpha[:1]) / np.linalg.norm(alpha[:1]))
+        split_v = 2 * n2 * N[0] * N[1] / (split_ms * 1e-3)
+        line["split"] = {"value": split_v, "unit": UNIT, "nrhs": n2, "ms_per_step": split_ms, "ranks": T2.ranks,
+                         "rel_err_forward": err2, "rel_err_inverse_of_forward": err2i, "dtype": "f32x2 (f64 io)"}
+        del x2, f2, y2
+        T2.close()
+
+        # plain FP64 r^2-FFT path (cuFFT Z2Z), one right-hand side
+        Tp = Transform(N, [p[0] for p in AB], [p[1] for p in AB], eps=1e-12, precision="fp64_plain")
+        xp = torch.tensor(alpha[:1], dtype=torch.float64, device=dev)
+        fp_ = torch.empty_like(xp)
+        yp = torch.empty_like(xp)
+        Tp.forward(xp, out=fp_)
+        Tp.inverse(fp_, out=yp)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        kp = 2
+        for _ in range(kp):
+            Tp.forward(xp, out=fp_)
+            Tp.inverse(fp_, out=yp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1) / kp
+        errp = float(np.linalg.norm(fp_.cpu().numpy() - ref) / np.linalg.norm(ref))
+        plain_v = 2 * N[0] * N[1] / (plain_ms * 1e-3)
+        line["plain_fp64"] = {"value": plain_v, "unit": UNIT, "nrhs": 1, "ms_per_step": plain_ms,
+                              "ranks": Tp.ranks, "rel_err_forward": errp,
+                              "speedup_fp32_over_plain": value / world / plain_v,
+                              "speedup_split_over_plain": split_v / plain_v}
+        Tp.close()
+
+        if world == 1:
+            line["cpu_baseline"] = oracle_throughput(nrhs)
+
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "jt.h"
@@ -82,9 +83,22 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
         }
     std::vector<Cx<R>> utab((size_t)r * n);
     for (size_t i = 0; i < utab.size(); ++i) utab[i] = Cx<R>{to_r(T.U[i].real(), tag), to_r(T.U[i].imag(), tag)};
-    std::vector<R> vblk((size_t)nu0 * n);
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t c = 0; c < nu0; ++c) vblk[(size_t)c * n + j] = to_r(T.Vblk[(size_t)j * nu0 + c], tag);
+    std::vector<R> vblk;
+    if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
+        // lane-major layout of the warp kernel: [c][t][e] <-> point j = t + T e, T = L / 16
+        const int64_t TT = L / 16;
+        vblk.assign((size_t)nu0 * L, to_r(0.0, tag));
+        for (int64_t c = 0; c < nu0; ++c)
+            for (int64_t t = 0; t < TT; ++t)
+                for (int64_t e = 0; e < 16; ++e) {
+                    int64_t j = t + TT * e;
+                    if (j < n) vblk[((size_t)c * TT + t) * 16 + e] = to_r(T.Vblk[(size_t)j * nu0 + c], tag);
+                }
+    } else {
+        vblk.assign((size_t)nu0 * n, to_r(0.0, tag));
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t c = 0; c < nu0; ++c) vblk[(size_t)c * n + j] = to_r(T.Vblk[(size_t)j * nu0 + c], tag);
+    }
     std::vector<Cx<R>> twid(L);
     const double twopi = 6.283185307179586476925286766559;
     for (int64_t q = 0; q < L; ++q) {

@@ -139,14 +139,30 @@ __device__ __forceinline__ Cx<R> twc(Cx<R> v) {
         if constexpr (8 * k == 3 * N) return mul_i(r);
         if constexpr (8 * k == 5 * N) return {-r.re, -r.im};
         return {r.im, -r.re};
+    } else if constexpr (N == 32 && (k & 1) == 0) {
+        return twc<k / 2, 16, R>(v);
     } else {
-        // remaining case: N = 16, k odd; e^{i pi k / 8} from cos(pi/8), sin(pi/8)
-        static_assert(N == 16 && (k & 1), "twiddle table covers radices up to 16");
-        constexpr double C8 = 0.92387953251128675612818318939678828682;
-        constexpr double S8 = 0.38268343236508977172845998403039886676;
-        constexpr double cr = (k == 1 || k == 15) ? C8 : (k == 3 || k == 13) ? S8 : (k == 5 || k == 11) ? -S8 : -C8;
-        constexpr double ci = (k == 1 || k == 7) ? S8 : (k == 3 || k == 5) ? C8 : (k == 9 || k == 15) ? -S8 : -C8;
-        const Cx<R> w{rc<R>(cr), rc<R>(ci)};
+        // remaining cases: N = 16 or 32 with k odd, from the first-octant values of
+        // cos and sin of multiples of pi/16 and the symmetries of the circle
+        static_assert((N == 16 || N == 32) && (k & 1), "twiddle table covers radices up to 32");
+        constexpr int k32 = (N == 16) ? 2 * k : k;  // angle = 2 pi k32 / 32
+        constexpr double C[9] = {1.0,
+                                 0.98078528040323044912618223613424033391,
+                                 0.92387953251128675612818318939678828682,
+                                 0.83146961230254523707878837761790575673,
+                                 0.70710678118654752440084436210484903928,
+                                 0.55557023301960222474283081394853287438,
+                                 0.38268343236508977172845998403039886676,
+                                 0.19509032201612826784828486847702224467,
+                                 0.0};
+        // cos(2 pi q / 32) for any q, from C[] with C[i] = cos(i pi / 16), i = 0..8
+        constexpr int q = k32 % 32;
+        constexpr int qc = (q <= 8) ? q : (q <= 16) ? 16 - q : (q <= 24) ? q - 16 : 32 - q;
+        constexpr double cs = (q <= 8 || q >= 24) ? C[qc] : -C[qc];
+        constexpr int qs = (q + 24) % 32;  // sin(x) = cos(x - pi/2)
+        constexpr int qsc = (qs <= 8) ? qs : (qs <= 16) ? 16 - qs : (qs <= 24) ? qs - 16 : 32 - qs;
+        constexpr double sn = (qs <= 8 || qs >= 24) ? C[qsc] : -C[qsc];
+        const Cx<R> w{rc<R>(cs), rc<R>(sn)};
         return cmul(v, w);
     }
 }

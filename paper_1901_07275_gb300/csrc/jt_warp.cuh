@@ -1,0 +1,349 @@
+// Warp-level fused axis kernel for FFT lengths L = 16 T, T in {1, 2, 4, 8, 16, 32}
+// (L = 16 .. 512), FP32.  One group of T lanes owns one fibre; a warp holds 32 / T fibres.
+//
+// The length-L inverse DFT (sign +) is split in four steps, L = 16 x T: with input index
+// p = t + T s (lane t < T holds s = 0..15 in registers) and output index m = k1 + 16 k2,
+//     Y[k1 + 16 k2] = sum_t w_T^{t k2} * ( w_L^{t k1} * sum_s x[t + T s] w_16^{s k1} ).
+// Step A (a 16-point DFT over s) and the twiddle w_L^{t k1} stay in registers -- the 15
+// twiddles of a lane never change, so they are loaded once per kernel.  One exchange
+// through shared memory regroups the values by k1, and step B finishes the T-point DFTs:
+// for T <= 16 each lane owns 16/T whole problems; for T = 32 each problem is split over a
+// lane pair (16-point DFTs on the even and odd lanes, then one radix-2 stage through a
+// shuffle).  The forward keeps only the outputs m <= L/2 that the gather can use.
+//
+// Fibres of a strided axis are staged through a shared-memory tile so that every global
+// load and store touches whole 32-byte sectors.
+#pragma once
+
+#include "jt_axis.cuh"
+
+namespace jt {
+namespace dev {
+
+template <int LOG2L>
+struct WShape {
+    static constexpr int L = 1 << LOG2L;
+    static constexpr int E = 16;
+    static constexpr int T = L / E;          // lanes per fibre
+    static constexpr int FPW = 32 / T;       // fibres per warp
+    static constexpr int WARPS = 8;
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int FT = WARPS * FPW;   // fibres per CTA iteration
+    static constexpr int XROW = T + 1;       // exchange buffer row (float2), padded
+    static constexpr int XBUF = 16 * XROW;   // exchange buffer per fibre (float2)
+    static constexpr int YBUF = L / 2 + 1 + ((L / 2) >> 5) + 1;  // gather buffer (float2)
+    static constexpr int BUF = (XBUF > YBUF ? XBUF : YBUF);
+    static constexpr int AUX = L;                               // per fibre: alpha_V / g (floats)
+    static constexpr int TROW = L + 1;                          // staging tile row (floats)
+    static __host__ __device__ constexpr int ypad(int m) { return m + (m >> 5); }
+};
+
+template <int LOG2L>
+constexpr size_t warp_smem_bytes(bool strided) {
+    using S = WShape<LOG2L>;
+    size_t b = (size_t)S::FT * (S::BUF * 8 + S::AUX * 4);
+    if (strided) b += (size_t)S::FT * S::TROW * 4;
+    return b;
+}
+
+__device__ __forceinline__ float2 f2(Cx<float> c) { return make_float2(c.re, c.im); }
+__device__ __forceinline__ Cx<float> cx(float2 v) { return Cx<float>{v.x, v.y}; }
+
+// Output ownership after step B.  Forward keeps m <= L/2; adjoint keeps all L.
+template <int LOG2L, bool FWD>
+struct Own {
+    using S = WShape<LOG2L>;
+    static constexpr int T = S::T;
+    // number of outputs a lane holds
+    static constexpr int NOUT = (T == 32) ? 16 : 16;
+    // index of output slot o of lane t
+    static __device__ __forceinline__ int idx(int t, int o) {
+        if constexpr (T == 32) {
+            const int k1 = t >> 1, h = t & 1;
+            return k1 + 16 * (h * 8 + (o & 7)) + (o >> 3) * (S::L / 2);  // o < 8: g = 0, o >= 8: g = 1
+        } else {
+            constexpr int P = 16 / T;  // problems per lane
+            const int q = o / T, k2 = o % T;
+            return (t * P + q) + 16 * k2;
+        }
+    }
+};
+
+// One forward or adjoint sweep over nfib fibres (see jt_axis.cuh for the operator).
+template <int LOG2L, bool FWD, bool STRIDED>
+__global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
+    warp_axis_kernel(AxisDev A, const float* in, float* out, long long nfib, long long inner) {
+    using S = WShape<LOG2L>;
+    constexpr int L = S::L, T = S::T, FT = S::FT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int fl = warp * S::FPW + lane / T;  // fibre slot in the CTA tile
+    const int t = lane % T;
+    float2* buf = reinterpret_cast<float2*>(smem_raw) + (size_t)fl * S::BUF;
+    float* aux = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)fl * S::AUX;
+    float* tile = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)FT * S::AUX;
+
+    const int n = A.n, nu0 = A.nu0, rank = A.rank;
+    const float2* __restrict__ vtab = reinterpret_cast<const float2*>(A.vtab);
+    const float2* __restrict__ utab = reinterpret_cast<const float2*>(A.utab);
+    const float* __restrict__ vblk = reinterpret_cast<const float*>(A.vblk);  // [c][t][e] layout
+    const float2* __restrict__ tw = reinterpret_cast<const float2*>(A.twid);
+
+    // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane
+    Cx<float> twA[16];
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) twA[k1] = cx(__ldg(tw + ((t * k1) & (L - 1))));
+
+    const long long ntiles = (nfib + FT - 1) / FT;
+    for (long long tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
+        const long long f0 = tile_i * FT;
+        const long long f = f0 + fl;
+        const bool valid = f < nfib;
+        float val[16];
+        if constexpr (STRIDED) {
+            __syncthreads();  // previous tile's stores done with the tile buffer
+            for (int i = threadIdx.x; i < FT * n; i += S::THREADS) {
+                const int ql = i % FT, row = i / FT;
+                const long long ff = f0 + ql;
+                float v = 0.0f;
+                if (ff < nfib) {
+                    const long long o = ff / inner, q = ff - o * inner;
+                    v = in[o * (long long)n * inner + q + (long long)row * inner];
+                }
+                tile[ql * S::TROW + row] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                int p = t + T * s;
+                val[s] = (p < n) ? tile[fl * S::TROW + p] : 0.0f;
+            }
+        } else {
+            const long long base = f * (long long)n;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                int p = t + T * s;
+                val[s] = (valid && p < n) ? in[base + p] : 0.0f;
+            }
+        }
+
+        float acc[16];
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[o] = 0.0f;
+
+        __syncwarp();
+        if constexpr (FWD) {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                int p = t + T * s;
+                if (p < nu0) aux[p] = val[s];
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                int p = t + T * s;
+                if (p < n) aux[p] = val[s];
+            }
+        }
+        __syncwarp();
+
+        for (int k = 0; k < rank; ++k) {
+            Cx<float> x[16];
+            if constexpr (FWD) {
+                const float2* vk = vtab + (size_t)k * L;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    float2 v = __ldg(vk + t + T * s);
+                    x[s] = Cx<float>{v.x * val[s], v.y * val[s]};
+                }
+            } else {
+                // z[m] = sum_{j : m_j = m} u_k[j] g_j, only m <= L/2 can be reached
+                const float2* uk = utab + (size_t)k * n;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    int m = t + T * s;
+                    Cx<float> z{0.0f, 0.0f};
+                    if (m <= L / 2) {
+                        int p1 = __ldg(A.bin_ptr + m), p2 = __ldg(A.bin_ptr + m + 1);
+                        for (int p = p1; p < p2; ++p) {
+                            int j = __ldg(A.bin_idx + p);
+                            float2 u = __ldg(uk + j);
+                            float g = aux[j];
+                            z.re = fmaf(u.x, g, z.re);
+                            z.im = fmaf(u.y, g, z.im);
+                        }
+                    }
+                    x[s] = z;
+                }
+            }
+            // step A: 16-point DFT over s, then the per-lane twiddles
+            dft<16, float>(x);
+#pragma unroll
+            for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], twA[k1]);
+            // exchange: buf[k1][t]
+            __syncwarp();
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) buf[k1 * S::XROW + t] = f2(x[k1]);
+            __syncwarp();
+            Cx<float> y[16];  // step-B outputs in Own<> order
+            if constexpr (T == 32) {
+                const int k1 = t >> 1, h = t & 1;
+                Cx<float> a[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) a[q] = cx(buf[k1 * S::XROW + 2 * q + h]);
+                dft<16, float>(a);
+                // odd lanes: twiddle w_32^{k2'}
+                if (h) {
+                    a[1] = twc<1, 32, float>(a[1]);
+                    a[2] = twc<2, 32, float>(a[2]);
+                    a[3] = twc<3, 32, float>(a[3]);
+                    a[4] = twc<4, 32, float>(a[4]);
+                    a[5] = twc<5, 32, float>(a[5]);
+                    a[6] = twc<6, 32, float>(a[6]);
+                    a[7] = twc<7, 32, float>(a[7]);
+                    a[8] = twc<8, 32, float>(a[8]);
+                    a[9] = twc<9, 32, float>(a[9]);
+                    a[10] = twc<10, 32, float>(a[10]);
+                    a[11] = twc<11, 32, float>(a[11]);
+                    a[12] = twc<12, 32, float>(a[12]);
+                    a[13] = twc<13, 32, float>(a[13]);
+                    a[14] = twc<14, 32, float>(a[14]);
+                    a[15] = twc<15, 32, float>(a[15]);
+                }
+                // radix-2 across the lane pair: lane h keeps k2' in [8h, 8h + 8)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    Cx<float> send = h ? a[i] : a[8 + i];
+                    Cx<float> own = h ? a[8 + i] : a[i];
+                    Cx<float> recv{__shfl_xor_sync(0xffffffffu, send.re, 1), __shfl_xor_sync(0xffffffffu, send.im, 1)};
+                    // B_0 + B_1 and B_0 - B_1 (own is B_h, recv is B_{1-h})
+                    y[i] = own + recv;
+                    Cx<float> d = own - recv;
+                    y[8 + i] = h ? Cx<float>{-d.re, -d.im} : d;
+                }
+            } else {
+                constexpr int P = 16 / T;
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    Cx<float> a[T];
+                    const int k1 = t * P + q;
+#pragma unroll
+                    for (int tt = 0; tt < T; ++tt) a[tt] = cx(buf[k1 * S::XROW + tt]);
+                    dft<T, float>(a);
+#pragma unroll
+                    for (int k2 = 0; k2 < T; ++k2) y[q * T + k2] = a[k2];
+                }
+            }
+            if constexpr (FWD) {
+                // Y[m] for m <= L/2 into the gather buffer, then acc_j += Re(u_k[j] Y[m_j])
+                __syncwarp();
+#pragma unroll
+                for (int o = 0; o < 16; ++o) {
+                    int m = Own<LOG2L, FWD>::idx(t, o);
+                    if (m <= L / 2) buf[S::ypad(m)] = f2(y[o]);
+                }
+                __syncwarp();
+                const float2* uk = utab + (size_t)k * n;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    int j = t + T * e;
+                    if (j < n) {
+                        int m = __ldg(A.mtab + j);
+                        float2 yy = buf[S::ypad(m)];
+                        float2 u = __ldg(uk + j);
+                        acc[e] = fmaf(u.x, yy.x, fmaf(-u.y, yy.y, acc[e]));
+                    }
+                }
+            } else {
+                const float2* vk = vtab + (size_t)k * L;
+#pragma unroll
+                for (int o = 0; o < 16; ++o) {
+                    int nu = Own<LOG2L, FWD>::idx(t, o);
+                    float2 v = __ldg(vk + nu);
+                    acc[o] = fmaf(v.x, y[o].re, fmaf(-v.y, y[o].im, acc[o]));
+                }
+            }
+        }
+
+        // dense low-degree block, vblk in [c][t][e] layout (16 floats per lane and degree)
+        const float4* vb4 = reinterpret_cast<const float4*>(vblk);
+        if constexpr (FWD) {
+            for (int c = 0; c < nu0; ++c) {
+                float ac = aux[c];
+                const float4* row = vb4 + ((size_t)c * T + t) * 4;
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    float4 v = __ldg(row + q4);
+                    acc[4 * q4 + 0] = fmaf(v.x, ac, acc[4 * q4 + 0]);
+                    acc[4 * q4 + 1] = fmaf(v.y, ac, acc[4 * q4 + 1]);
+                    acc[4 * q4 + 2] = fmaf(v.z, ac, acc[4 * q4 + 2]);
+                    acc[4 * q4 + 3] = fmaf(v.w, ac, acc[4 * q4 + 3]);
+                }
+            }
+        } else {
+            // alpha_c = sum_j vblk[c][j] g_j: lane partials, then a butterfly sum over the group
+            for (int c = 0; c < nu0; ++c) {
+                const float4* row = vb4 + ((size_t)c * T + t) * 4;
+                float part = 0.0f;
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    float4 v = __ldg(row + q4);
+                    part = fmaf(v.x, val[4 * q4 + 0], part);
+                    part = fmaf(v.y, val[4 * q4 + 1], part);
+                    part = fmaf(v.z, val[4 * q4 + 2], part);
+                    part = fmaf(v.w, val[4 * q4 + 3], part);
+                }
+#pragma unroll
+                for (int off = T / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+#pragma unroll
+                for (int o = 0; o < 16; ++o)
+                    if (Own<LOG2L, FWD>::idx(t, o) == c) acc[o] = part;
+            }
+        }
+
+        // store
+        if constexpr (STRIDED) {
+            __syncthreads();
+            if constexpr (FWD) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    int j = t + T * e;
+                    if (j < n) tile[fl * S::TROW + j] = acc[e];
+                }
+            } else {
+#pragma unroll
+                for (int o = 0; o < 16; ++o) {
+                    int nu = Own<LOG2L, FWD>::idx(t, o);
+                    if (nu < n) tile[fl * S::TROW + nu] = acc[o];
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < FT * n; i += S::THREADS) {
+                const int ql = i % FT, row = i / FT;
+                const long long ff = f0 + ql;
+                if (ff < nfib) {
+                    const long long o = ff / inner, q = ff - o * inner;
+                    out[o * (long long)n * inner + q + (long long)row * inner] = tile[ql * S::TROW + row];
+                }
+            }
+        } else if (valid) {
+            const long long base = f * (long long)n;
+            if constexpr (FWD) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    int j = t + T * e;
+                    if (j < n) out[base + j] = acc[e];
+                }
+            } else {
+#pragma unroll
+                for (int o = 0; o < 16; ++o) {
+                    int nu = Own<LOG2L, FWD>::idx(t, o);
+                    if (nu < n) out[base + nu] = acc[o];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace jt
