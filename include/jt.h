@@ -64,7 +64,7 @@ typedef enum {
 
 typedef struct {
     int32_t prec;           /* jt_precision */
-    int32_t nu0;            /* split degree of Eq. tf:jn; default 27 */
+    int32_t nu0;            /* split degree of Eq. tf:jn, 0..32; default 27 */
     int32_t rank_cap;       /* largest rank allowed per axis; 0 => max(ceil(2 log2 n), 64) */
     int32_t oversample_q;   /* oversampling factor q of Algorithm 2.1; default 3 */
     uint64_t seed;          /* seed of the row/column sampling in Algorithm 2.1 */

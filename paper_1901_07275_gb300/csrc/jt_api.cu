@@ -85,15 +85,10 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     for (size_t i = 0; i < utab.size(); ++i) utab[i] = Cx<R>{to_r(T.U[i].real(), tag), to_r(T.U[i].imag(), tag)};
     std::vector<R> vblk;
     if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
-        // lane-major layout of the warp kernel: [c][t][e] <-> point j = t + T e, T = L / 16
-        const int64_t TT = L / 16;
+        // rows padded to L with zeros (warp kernel)
         vblk.assign((size_t)nu0 * L, to_r(0.0, tag));
-        for (int64_t c = 0; c < nu0; ++c)
-            for (int64_t t = 0; t < TT; ++t)
-                for (int64_t e = 0; e < 16; ++e) {
-                    int64_t j = t + TT * e;
-                    if (j < n) vblk[((size_t)c * TT + t) * 16 + e] = to_r(T.Vblk[(size_t)j * nu0 + c], tag);
-                }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t c = 0; c < nu0; ++c) vblk[(size_t)c * L + j] = to_r(T.Vblk[(size_t)j * nu0 + c], tag);
     } else {
         vblk.assign((size_t)nu0 * n, to_r(0.0, tag));
         for (int64_t j = 0; j < n; ++j)
@@ -119,6 +114,9 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     A.L = (int)L;
     A.nu0 = (int)nu0;
     A.rank = (int)r;
+    A.sorted = 1;
+    for (int64_t j = 1; j < n; ++j)
+        if (T.m[j] < T.m[j - 1]) A.sorted = 0;
     jt_status st;
     const void* p;
     if ((st = upload(ax, vtab, &A.vtab, s)) != JT_OK) return st;

@@ -253,6 +253,7 @@ struct Shape {
 // Tables of one axis on the device (all owned by the plan).
 struct AxisDev {
     int n, L, nu0, rank;
+    int sorted;          // 1 if m_j is non-decreasing in j (bin_idx is the identity)
     const void* vtab;    // rank x L   Cx<R>: v_k at bins nu0..n-1, zero elsewhere
     const void* utab;    // rank x n   Cx<R>: sqrt(w_j) u_k[j]
     const int* mtab;     // n          FFT bin of point j

@@ -17,6 +17,11 @@
 
 #include "jt_axis.cuh"
 
+// CTAs per SM the register allocation is sized for (2 => at most 128 registers a thread).
+#ifndef JT_WARP_MINB
+#define JT_WARP_MINB 2
+#endif
+
 namespace jt {
 namespace dev {
 
@@ -29,13 +34,20 @@ struct WShape {
     static constexpr int WARPS = 8;
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int FT = WARPS * FPW;   // fibres per CTA iteration
-    static constexpr int XROW = T + 1;       // exchange buffer row (float2), padded
+    // Exchange rows are padded so that the 64-bit accesses of a half-warp never share a bank:
+    // row k1 starts at k1 * XROW float2; T = 32 reads (k1 = t/2, column 2q + h) need an even
+    // pad, T <= 16 reads (k1 = t) an odd one.
+    static constexpr int XROW = (T == 32) ? T + 2 : T + 1;
     static constexpr int XBUF = 16 * XROW;   // exchange buffer per fibre (float2)
-    static constexpr int YBUF = L / 2 + 1 + ((L / 2) >> 5) + 1;  // gather buffer (float2)
+    static constexpr int YBUF = L / 2 + 1 + ((L / 2) >> 4) + 1;  // gather buffer (float2)
     static constexpr int BUF = (XBUF > YBUF ? XBUF : YBUF);
-    static constexpr int AUX = L;                               // per fibre: alpha_V / g (floats)
-    static constexpr int TROW = L + 1;                          // staging tile row (floats)
-    static __host__ __device__ constexpr int ypad(int m) { return m + (m >> 5); }
+    static constexpr int AUX = L + L / 16 + 1;                  // per fibre: alpha_V / g (floats)
+    // staging tile rows: consecutive threads cover FT fibres x (32 / FT) rows
+    static constexpr int TROW = L + ((FT >= 32) ? 1 : 32 / FT);
+    // gather buffer index: a half-warp writes runs m0 + [0, 8) and m0 + 128 + [0, 8)
+    static __host__ __device__ constexpr int ypad(int m) { return m + (m >> 4); }
+    // adjoint copy of g: a lane reads points ~2m, stride 2 across lanes
+    static __host__ __device__ constexpr int apad(int j) { return j + (j >> 4); }
 };
 
 template <int LOG2L>
@@ -71,7 +83,7 @@ struct Own {
 
 // One forward or adjoint sweep over nfib fibres (see jt_axis.cuh for the operator).
 template <int LOG2L, bool FWD, bool STRIDED>
-__global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
+__global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     warp_axis_kernel(AxisDev A, const float* in, float* out, long long nfib, long long inner) {
     using S = WShape<LOG2L>;
     constexpr int L = S::L, T = S::T, FT = S::FT;
@@ -86,13 +98,35 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
     const int n = A.n, nu0 = A.nu0, rank = A.rank;
     const float2* __restrict__ vtab = reinterpret_cast<const float2*>(A.vtab);
     const float2* __restrict__ utab = reinterpret_cast<const float2*>(A.utab);
-    const float* __restrict__ vblk = reinterpret_cast<const float*>(A.vblk);  // [c][t][e] layout
+    const float* __restrict__ vblk = reinterpret_cast<const float*>(A.vblk);  // [c][0..L), zero beyond n
     const float2* __restrict__ tw = reinterpret_cast<const float2*>(A.twid);
 
     // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane
     Cx<float> twA[16];
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) twA[k1] = cx(__ldg(tw + ((t * k1) & (L - 1))));
+    // Per-lane constants.  Forward: padded gather-buffer index of each owned point, two
+    // 16-bit fields a word.  Adjoint: first and one-past-last point of each owned bin.
+    constexpr int NPK = FWD ? 8 : 16;
+    unsigned pk[NPK];
+#pragma unroll
+    for (int i = 0; i < NPK; ++i) {
+        if constexpr (FWD) {
+            unsigned v[2] = {0u, 0u};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = t + T * (2 * i + h);
+                if (j < n) v[h] = (unsigned)S::ypad(__ldg(A.mtab + j));
+            }
+            pk[i] = v[0] | (v[1] << 16);
+        } else {
+            const int m = t + T * i;
+            unsigned v = 0;
+            if (m <= L / 2) v = (unsigned)__ldg(A.bin_ptr + m) | ((unsigned)__ldg(A.bin_ptr + m + 1) << 16);
+            pk[i] = v;
+        }
+    }
+    const bool sorted = A.sorted != 0;
 
     const long long ntiles = (nfib + FT - 1) / FT;
     for (long long tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
@@ -128,10 +162,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
         }
 
         float acc[16];
-#pragma unroll
-        for (int o = 0; o < 16; ++o) acc[o] = 0.0f;
-
-        __syncwarp();
+        __syncthreads();  // the previous tile is done with aux and the exchange region
         if constexpr (FWD) {
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
@@ -142,10 +173,80 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 int p = t + T * s;
-                if (p < n) aux[p] = val[s];
+                if (p < n) aux[S::apad(p)] = val[s];
             }
         }
-        __syncwarp();
+        __syncthreads();
+        // Dense low-degree block for the whole tile at once, so that each row of the table
+        // (vblk[c][0..L), zero beyond n) is read once per tile rather than once per fibre.
+        // The exchange region is free until the rank loop and holds the results meanwhile.
+        float* vres = reinterpret_cast<float*>(smem_raw);
+        const float* __restrict__ auxbase =
+            reinterpret_cast<const float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF);
+        if constexpr (FWD) {
+            // FT x L outputs, 16 per thread: JPT points x FPT fibres
+            constexpr int JPT = (L > 256) ? L / 256 : 1;
+            constexpr int FPT = 16 / JPT;
+            constexpr int FSTEP = (L >= 256) ? 1 : 256 / L;
+            const int j0 = threadIdx.x % (L < 256 ? L : 256);
+            const int fb = (L >= 256) ? 0 : threadIdx.x / L;
+            float part[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) part[i] = 0.0f;
+            for (int c = 0; c < nu0; ++c) {
+                float vj[JPT];
+#pragma unroll
+                for (int jj = 0; jj < JPT; ++jj) vj[jj] = __ldg(vblk + (size_t)c * L + j0 + 256 * jj);
+#pragma unroll
+                for (int ff = 0; ff < FPT; ++ff) {
+                    const float a = auxbase[(size_t)(fb + FSTEP * ff) * S::AUX + c];
+#pragma unroll
+                    for (int jj = 0; jj < JPT; ++jj) part[ff * JPT + jj] = fmaf(vj[jj], a, part[ff * JPT + jj]);
+                }
+            }
+#pragma unroll
+            for (int ff = 0; ff < FPT; ++ff)
+#pragma unroll
+                for (int jj = 0; jj < JPT; ++jj) vres[(fb + FSTEP * ff) * L + j0 + 256 * jj] = part[ff * JPT + jj];
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[e] = vres[fl * L + t + T * e];
+        } else {
+            // alpha_c(fibre) = sum_j vblk[c][j] g_j: warp w takes (fibre chunk, degree) items,
+            // lanes split the points, partials for 8 fibres at a time, then a warp sum
+            constexpr int NCH = (FT + 7) / 8;
+            for (int item = warp; item < NCH * nu0; item += S::WARPS) {
+                const int ch = item / nu0, c = item % nu0;
+                float part[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) part[i] = 0.0f;
+                for (int j = lane; j < L; j += 32) {
+                    const float v = __ldg(vblk + (size_t)c * L + j);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int ff = ch * 8 + i;
+                        if (ff < FT) part[i] = fmaf(v, auxbase[(size_t)ff * S::AUX + S::apad(j)], part[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) part[i] += __shfl_xor_sync(0xffffffffu, part[i], off);
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (ch * 8 + i < FT) vres[(ch * 8 + i) * 32 + c] = part[i];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < 16; ++o) {
+                const int nu = Own<LOG2L, FWD>::idx(t, o);
+                acc[o] = (nu < nu0) ? vres[fl * 32 + nu] : 0.0f;
+            }
+        }
+        __syncthreads();  // results read before the rank loop reuses the exchange region
 
         for (int k = 0; k < rank; ++k) {
             Cx<float> x[16];
@@ -157,18 +258,25 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
                     x[s] = Cx<float>{v.x * val[s], v.y * val[s]};
                 }
             } else {
-                // z[m] = sum_{j : m_j = m} u_k[j] g_j, only m <= L/2 can be reached
+                // z[m] = sum_{j : m_j = m} u_k[j] g_j, only m <= L/2 can be reached; with the
+                // points in bin order (always so for Gauss--Jacobi nodes) point p of a bin is j = p
                 const float2* uk = utab + (size_t)k * n;
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
-                    int m = t + T * s;
+                    const int p1 = (int)(pk[s] & 0xffffu), p2 = (int)(pk[s] >> 16);
                     Cx<float> z{0.0f, 0.0f};
-                    if (m <= L / 2) {
-                        int p1 = __ldg(A.bin_ptr + m), p2 = __ldg(A.bin_ptr + m + 1);
+                    if (sorted) {
+                        for (int p = p1; p < p2; ++p) {
+                            float2 u = __ldg(uk + p);
+                            float g = aux[S::apad(p)];
+                            z.re = fmaf(u.x, g, z.re);
+                            z.im = fmaf(u.y, g, z.im);
+                        }
+                    } else {
                         for (int p = p1; p < p2; ++p) {
                             int j = __ldg(A.bin_idx + p);
                             float2 u = __ldg(uk + j);
-                            float g = aux[j];
+                            float g = aux[S::apad(j)];
                             z.re = fmaf(u.x, g, z.re);
                             z.im = fmaf(u.y, g, z.im);
                         }
@@ -248,8 +356,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
                 for (int e = 0; e < 16; ++e) {
                     int j = t + T * e;
                     if (j < n) {
-                        int m = __ldg(A.mtab + j);
-                        float2 yy = buf[S::ypad(m)];
+                        const unsigned ym = (e & 1) ? (pk[e >> 1] >> 16) : (pk[e >> 1] & 0xffffu);
+                        float2 yy = buf[ym];
                         float2 u = __ldg(uk + j);
                         acc[e] = fmaf(u.x, yy.x, fmaf(-u.y, yy.y, acc[e]));
                     }
@@ -262,42 +370,6 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, 2)
                     float2 v = __ldg(vk + nu);
                     acc[o] = fmaf(v.x, y[o].re, fmaf(-v.y, y[o].im, acc[o]));
                 }
-            }
-        }
-
-        // dense low-degree block, vblk in [c][t][e] layout (16 floats per lane and degree)
-        const float4* vb4 = reinterpret_cast<const float4*>(vblk);
-        if constexpr (FWD) {
-            for (int c = 0; c < nu0; ++c) {
-                float ac = aux[c];
-                const float4* row = vb4 + ((size_t)c * T + t) * 4;
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    float4 v = __ldg(row + q4);
-                    acc[4 * q4 + 0] = fmaf(v.x, ac, acc[4 * q4 + 0]);
-                    acc[4 * q4 + 1] = fmaf(v.y, ac, acc[4 * q4 + 1]);
-                    acc[4 * q4 + 2] = fmaf(v.z, ac, acc[4 * q4 + 2]);
-                    acc[4 * q4 + 3] = fmaf(v.w, ac, acc[4 * q4 + 3]);
-                }
-            }
-        } else {
-            // alpha_c = sum_j vblk[c][j] g_j: lane partials, then a butterfly sum over the group
-            for (int c = 0; c < nu0; ++c) {
-                const float4* row = vb4 + ((size_t)c * T + t) * 4;
-                float part = 0.0f;
-#pragma unroll
-                for (int q4 = 0; q4 < 4; ++q4) {
-                    float4 v = __ldg(row + q4);
-                    part = fmaf(v.x, val[4 * q4 + 0], part);
-                    part = fmaf(v.y, val[4 * q4 + 1], part);
-                    part = fmaf(v.z, val[4 * q4 + 2], part);
-                    part = fmaf(v.w, val[4 * q4 + 3], part);
-                }
-#pragma unroll
-                for (int off = T / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-#pragma unroll
-                for (int o = 0; o < 16; ++o)
-                    if (Own<LOG2L, FWD>::idx(t, o) == c) acc[o] = part;
             }
         }
 
