@@ -41,13 +41,14 @@ struct WShape {
     static constexpr int XBUF = 16 * XROW;   // exchange buffer per fibre (float2)
     static constexpr int YBUF = L / 2 + 1 + ((L / 2) >> 4) + 1;  // gather buffer (float2)
     static constexpr int BUF = (XBUF > YBUF ? XBUF : YBUF);
-    static constexpr int AUX = L + L / 16 + 1;                  // per fibre: alpha_V / g (floats)
+    static constexpr int AUX = L + L / 32 + 1;                  // per fibre: alpha_V / g (floats)
     // staging tile rows: consecutive threads cover FT fibres x (32 / FT) rows
     static constexpr int TROW = L + ((FT >= 32) ? 1 : 32 / FT);
     // gather buffer index: a half-warp writes runs m0 + [0, 8) and m0 + 128 + [0, 8)
     static __host__ __device__ constexpr int ypad(int m) { return m + (m >> 4); }
-    // adjoint copy of g: a lane reads points ~2m, stride 2 across lanes
-    static __host__ __device__ constexpr int apad(int j) { return j + (j >> 4); }
+    // adjoint copy of g: lanes read points ~2t (stride 2) in the scatter and consecutive
+    // points in the dense block; j + j/32 keeps both patterns free of bank conflicts
+    static __host__ __device__ constexpr int apad(int j) { return j + (j >> 5); }
 };
 
 template <int LOG2L>
@@ -136,15 +137,17 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         float val[16];
         if constexpr (STRIDED) {
             __syncthreads();  // previous tile's stores done with the tile buffer
-            for (int i = threadIdx.x; i < FT * n; i += S::THREADS) {
-                const int ql = i % FT, row = i / FT;
+            {
+                // FT divides the CTA size, so each thread always serves the same fibre ql
+                const int ql = threadIdx.x % FT;
                 const long long ff = f0 + ql;
-                float v = 0.0f;
+                long long gbase = 0;
                 if (ff < nfib) {
                     const long long o = ff / inner, q = ff - o * inner;
-                    v = in[o * (long long)n * inner + q + (long long)row * inner];
+                    gbase = o * (long long)n * inner + q;
                 }
-                tile[ql * S::TROW + row] = v;
+                for (int row = threadIdx.x / FT; row < n; row += S::THREADS / FT)
+                    tile[ql * S::TROW + row] = (ff < nfib) ? in[gbase + (long long)row * inner] : 0.0f;
             }
             __syncthreads();
 #pragma unroll
@@ -265,21 +268,28 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 for (int s = 0; s < 16; ++s) {
                     const int p1 = (int)(pk[s] & 0xffffu), p2 = (int)(pk[s] >> 16);
                     Cx<float> z{0.0f, 0.0f};
-                    if (sorted) {
-                        for (int p = p1; p < p2; ++p) {
-                            float2 u = __ldg(uk + p);
-                            float g = aux[S::apad(p)];
-                            z.re = fmaf(u.x, g, z.re);
-                            z.im = fmaf(u.y, g, z.im);
-                        }
-                    } else {
-                        for (int p = p1; p < p2; ++p) {
-                            int j = __ldg(A.bin_idx + p);
-                            float2 u = __ldg(uk + j);
-                            float g = aux[S::apad(j)];
-                            z.re = fmaf(u.x, g, z.re);
-                            z.im = fmaf(u.y, g, z.im);
-                        }
+                    // bins hold about two points: the first two are loaded without a loop so
+                    // that every lane issues all its loads at once; larger bins finish below
+                    const int j0 = sorted ? p1 : __ldg(A.bin_idx + min(p1, n - 1));
+                    const int j1 = sorted ? p1 + 1 : __ldg(A.bin_idx + min(p1 + 1, n - 1));
+                    if (p1 < p2) {
+                        float2 u = __ldg(uk + j0);
+                        float g = aux[S::apad(j0)];
+                        z.re = u.x * g;
+                        z.im = u.y * g;
+                    }
+                    if (p1 + 1 < p2) {
+                        float2 u = __ldg(uk + j1);
+                        float g = aux[S::apad(j1)];
+                        z.re = fmaf(u.x, g, z.re);
+                        z.im = fmaf(u.y, g, z.im);
+                    }
+                    for (int p = p1 + 2; p < p2; ++p) {
+                        int j = sorted ? p : __ldg(A.bin_idx + p);
+                        float2 u = __ldg(uk + j);
+                        float g = aux[S::apad(j)];
+                        z.re = fmaf(u.x, g, z.re);
+                        z.im = fmaf(u.y, g, z.im);
                     }
                     x[s] = z;
                 }
@@ -390,12 +400,14 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 }
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < FT * n; i += S::THREADS) {
-                const int ql = i % FT, row = i / FT;
+            {
+                const int ql = threadIdx.x % FT;
                 const long long ff = f0 + ql;
                 if (ff < nfib) {
                     const long long o = ff / inner, q = ff - o * inner;
-                    out[o * (long long)n * inner + q + (long long)row * inner] = tile[ql * S::TROW + row];
+                    const long long gbase = o * (long long)n * inner + q;
+                    for (int row = threadIdx.x / FT; row < n; row += S::THREADS / FT)
+                        out[gbase + (long long)row * inner] = tile[ql * S::TROW + row];
                 }
             }
         } else if (valid) {
