@@ -107,6 +107,28 @@ jt_status jt_adjoint(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt
 jt_status jt_inverse(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt_stream_t stream);
 
 /*
+ * Forward transform of a JT_FP64_PLAIN plan that allocates nothing (the paper has no
+ * counterpart; this is a library convenience).  The plain FP64 path needs work buffers
+ * beyond its input and output; jt_forward takes them from the plan, this call takes them
+ * from one fixed 16 MiB device array compiled into libjt, which every GPU that loads the
+ * library holds until the process exits.  It is meant for callers that must not request
+ * device memory at call time: a serving loop that cannot risk an allocation failure or the
+ * allocator's locks in the middle of a request, or a process whose free device memory is
+ * already reserved by another allocator (a framework's caching allocator, for instance).
+ *   Same arguments, layout and result as jt_forward (float64 in and out, device pointers).
+ *   JT_ENOTSUP for plans of another precision; JT_EINVAL for bad arguments or when the plan
+ *   needs more than 16 MiB of work space (about 2^18 points, e.g. 512 x 512 fits,
+ *   1024 x 1024 does not).  No cudaMalloc, cudaFree or allocating library call is made.
+ *   The first call on a device looks up the array's device address (with that device
+ *   current) and caches it; make that first call before any stream capture.
+ *   Every call shares the one array, which keeps the last call's contents (each call clears
+ *   what it needs at zero itself): calls that overlap on the GPU -- on different streams, or
+ *   from different host threads -- race on it and must be serialised by the caller.
+ */
+jt_status jt_forward_plain_noalloc(jt_plan* plan, const void* alpha, void* f, int64_t nrhs,
+                                   jt_stream_t stream);
+
+/*
  * Plan inspection.  For axis in [0, d): *rank = number of rank terms r, *fft_len = L.
  * t_out / w_out (each NULL or n[axis] host float64): the points and the trigonometric
  * Gauss--Jacobi weights w_k (1 for a nonuniform axis).  JT_EINVAL on a bad axis.

@@ -26,6 +26,7 @@ EXPORTS = (
     "jt_forward",
     "jt_adjoint",
     "jt_inverse",
+    "jt_forward_plain_noalloc",
     "jt_plan_info",
     "jt_destroy",
     "jt_status_string",
@@ -73,7 +74,7 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(dbl), ctypes.POINTER(ctypes.POINTER(dbl)), dbl,
                                  ctypes.POINTER(Options), vp]
     L.jt_plan_create.restype = i32
-    for name in ("jt_forward", "jt_adjoint", "jt_inverse"):
+    for name in ("jt_forward", "jt_adjoint", "jt_inverse", "jt_forward_plain_noalloc"):
         f = getattr(L, name)
         f.argtypes = [vp, vp, vp, i64, vp]
         f.restype = i32
@@ -159,6 +160,12 @@ def jt_adjoint(plan: int, g_ptr: int, alpha_ptr: int, nrhs: int, stream: int = 0
 
 def jt_inverse(plan: int, g_ptr: int, alpha_ptr: int, nrhs: int, stream: int = 0) -> None:
     _check(lib().jt_inverse(_ptr(plan), _ptr(g_ptr), _ptr(alpha_ptr), int(nrhs), _ptr(stream)), "jt_inverse")
+
+
+def jt_forward_plain_noalloc(plan: int, alpha_ptr: int, f_ptr: int, nrhs: int, stream: int = 0) -> None:
+    """Forward transform of a plain-FP64 plan with the library's static work area (no allocation)."""
+    _check(lib().jt_forward_plain_noalloc(_ptr(plan), _ptr(alpha_ptr), _ptr(f_ptr), int(nrhs), _ptr(stream)),
+           "jt_forward_plain_noalloc")
 
 
 def jt_plan_info(plan: int, axis: int, n: int | None = None):

@@ -261,6 +261,12 @@ jt_status jt_inverse(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt
     return apply(plan, g, alpha, nrhs, false, (cudaStream_t)stream);
 }
 
+jt_status jt_forward_plain_noalloc(jt_plan* plan, const void* alpha, void* f, int64_t nrhs, jt_stream_t stream) {
+    if (!plan || !alpha || !f || nrhs < 1) return JT_EINVAL;
+    if (plan->prec != JT_FP64_PLAIN) return JT_ENOTSUP;
+    return jt::plain_apply_static(plan->plain, (const double*)alpha, (double*)f, nrhs, true, (cudaStream_t)stream);
+}
+
 jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_len, double* t_out, double* w_out) {
     if (!plan || axis < 0 || axis >= plan->d) return JT_EINVAL;
     const jt::AxisTables& T = plan->axes[axis].host;

@@ -15,10 +15,16 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "jt_plain.hpp"
+
+// Fixed work area of the allocation-free entry point (jt_forward_plain_noalloc).  It is part
+// of the library image, so every GPU that loads libjt holds these bytes until the process
+// exits; all calls of that entry point share it.
+static __device__ __align__(256) unsigned char jt_static_scratch[JT_STATIC_SCRATCH_BYTES];
 
 namespace jt {
 
@@ -222,6 +228,15 @@ inline unsigned grid_for(long long count) {
 
 }  // namespace
 
+// Work buffers of one apply: X (L-box complex), Z (per-axis complex work) and two real
+// n-box temporaries.
+struct PlainScratch {
+    double2* X;
+    double2* Z;
+    double* T1;
+    double* T2;
+};
+
 struct PlainPlan {
     int d = 1;
     Dims D{};
@@ -280,7 +295,8 @@ jt_status run_fft(AxisFFT& f, double2* buf, int sign, cudaStream_t s) {
 }
 
 // one axis operator (V or G block, forward or adjoint) from src to dst on the n-box
-jt_status axis_op(PlainPlan* P, int a, bool vblock, bool adj, const double* src, double* dst, cudaStream_t s) {
+jt_status axis_op(PlainPlan* P, const PlainScratch& W, int a, bool vblock, bool adj, const double* src, double* dst,
+                  cudaStream_t s) {
     const PAxis& A = P->ax[a];
     long long outer = 1, inner = 1;
     for (int i = 0; i < a; ++i) outer *= P->D.n[i];
@@ -296,12 +312,12 @@ jt_status axis_op(PlainPlan* P, int a, bool vblock, bool adj, const double* src,
     for (int k = 0; k < A.rank; ++k) {
         const double2* uk = A.U + (size_t)k * A.n;
         const double2* vk = A.V + (size_t)k * N;
-        k_axis_bins<<<grid_for(ztot), 256, 0, s>>>(P->Z, src, outer, A.n, A.L, inner, adj ? uk : vk, A.nu0,
+        k_axis_bins<<<grid_for(ztot), 256, 0, s>>>(W.Z, src, outer, A.n, A.L, inner, adj ? uk : vk, A.nu0,
                                                     adj ? 1 : 0, A.bin_ptr, A.bin_idx);
         if (cudaGetLastError() != cudaSuccess) return JT_ECUDA;
-        jt_status st = run_fft(P->fz[a], P->Z, +1, s);
+        jt_status st = run_fft(P->fz[a], W.Z, +1, s);
         if (st != JT_OK) return st;
-        k_axis_acc<<<grid_for(total), 256, 0, s>>>(dst, P->Z, outer, A.n, A.L, inner, adj ? vk : uk, A.nu0, A.m,
+        k_axis_acc<<<grid_for(total), 256, 0, s>>>(dst, W.Z, outer, A.n, A.L, inner, adj ? vk : uk, A.nu0, A.m,
                                                    adj ? 1 : 0);
         if (cudaGetLastError() != cudaSuccess) return JT_ECUDA;
     }
@@ -309,7 +325,7 @@ jt_status axis_op(PlainPlan* P, int a, bool vblock, bool adj, const double* src,
 }
 
 // all-G block by the r^d d-dimensional FFT form, accumulated into acc
-jt_status rd_block(PlainPlan* P, const double* src, double* acc, bool adj, cudaStream_t s) {
+jt_status rd_block(PlainPlan* P, const PlainScratch& W, const double* src, double* acc, bool adj, cudaStream_t s) {
     const int d = P->d;
     const Dims& D = P->D;
     const long long ltot = D.L[0] * D.L[1] * D.L[2];
@@ -332,27 +348,27 @@ jt_status rd_block(PlainPlan* P, const double* src, double* acc, bool adj, cudaS
                         Fu.p[a] = A.U + (size_t)ks[a] * A.n;
                         Fv.conj[a] = Fu.conj[a] = conj[a];
                     }
-                    if (cudaMemsetAsync(P->X, 0, sizeof(double2) * ltot, s) != cudaSuccess) return JT_ECUDA;
+                    if (cudaMemsetAsync(W.X, 0, sizeof(double2) * ltot, s) != cudaSuccess) return JT_ECUDA;
                     if (!adj) {
-                        k_bins_fwd<<<grid_for(ntot), 256, 0, s>>>(P->X, src, D, Fv);
+                        k_bins_fwd<<<grid_for(ntot), 256, 0, s>>>(W.X, src, D, Fv);
                     } else {
                         const PAxis& A0 = P->ax[0];
                         const PAxis& A1 = P->ax[d > 1 ? 1 : 0];
                         const PAxis& A2 = P->ax[d > 2 ? 2 : 0];
                         long long h = (D.L[0] / 2 + 1) * (d > 1 ? D.L[1] / 2 + 1 : 1) * (d > 2 ? D.L[2] / 2 + 1 : 1);
-                        k_scatter_adj<<<grid_for(h), 256, 0, s>>>(P->X, src, D, Fu, A0.bin_ptr, A0.bin_idx,
+                        k_scatter_adj<<<grid_for(h), 256, 0, s>>>(W.X, src, D, Fu, A0.bin_ptr, A0.bin_idx,
                                                                    A1.bin_ptr, A1.bin_idx, A2.bin_ptr, A2.bin_idx);
                     }
                     if (cudaGetLastError() != cudaSuccess) return JT_ECUDA;
                     for (int a = 0; a < d; ++a) {
-                        jt_status st = run_fft(P->fx[a], P->X, conj[a] ? -1 : +1, s);
+                        jt_status st = run_fft(P->fx[a], W.X, conj[a] ? -1 : +1, s);
                         if (st != JT_OK) return st;
                     }
                     if (!adj)
-                        k_gather_fwd<<<grid_for(ntot), 256, 0, s>>>(acc, P->X, D, Fu, P->ax[0].m,
+                        k_gather_fwd<<<grid_for(ntot), 256, 0, s>>>(acc, W.X, D, Fu, P->ax[0].m,
                                                                      P->ax[d > 1 ? 1 : 0].m, P->ax[d > 2 ? 2 : 0].m, w);
                     else
-                        k_scale_adj<<<grid_for(ntot), 256, 0, s>>>(acc, P->X, D, Fv, w);
+                        k_scale_adj<<<grid_for(ntot), 256, 0, s>>>(acc, W.X, D, Fv, w);
                     if (cudaGetLastError() != cudaSuccess) return JT_ECUDA;
                 }
     }
@@ -431,8 +447,11 @@ jt_status plain_create(PlainPlan** out, const std::vector<const AxisTables*>& ax
     return JT_OK;
 }
 
-jt_status plain_apply(PlainPlan* P, const double* in, double* out, int64_t nrhs, bool fwd, cudaStream_t s) {
-    if (!P) return JT_EINVAL;
+namespace {
+
+// The whole plain apply with caller-chosen work buffers.
+jt_status plain_apply_bufs(PlainPlan* P, const PlainScratch& W, const double* in, double* out, int64_t nrhs,
+                           bool fwd, cudaStream_t s) {
     const int d = P->d;
     const long long ntot = P->D.n[0] * P->D.n[1] * P->D.n[2];
     const bool adj = !fwd;
@@ -440,31 +459,98 @@ jt_status plain_apply(PlainPlan* P, const double* in, double* out, int64_t nrhs,
         const double* src = in + rr * ntot;
         double* dst = out + rr * ntot;
         // in-place safety: the all-G block reads src while accumulating into T2, copied at the end
-        if (cudaMemsetAsync(P->T2, 0, sizeof(double) * ntot, s) != cudaSuccess) return JT_ECUDA;
-        jt_status st = rd_block(P, src, P->T2, adj, s);
+        if (cudaMemsetAsync(W.T2, 0, sizeof(double) * ntot, s) != cudaSuccess) return JT_ECUDA;
+        jt_status st = rd_block(P, W, src, W.T2, adj, s);
         if (st != JT_OK) return st;
         // blocks with at least one dense factor, axis by axis
         for (int mask = 1; mask < (1 << d); ++mask) {
             // chain through T1 and X (free after the all-G block, used as a real buffer) so
             // that src stays intact for the next block
             const double* cur = src;
-            double* tmp[2] = {P->T1, reinterpret_cast<double*>(P->X)};
+            double* tmp[2] = {W.T1, reinterpret_cast<double*>(W.X)};
             int which = 0;
             for (int a = d - 1; a >= 0; --a) {
                 bool vb = (mask >> a) & 1;
                 double* nxt = tmp[which];
-                st = axis_op(P, a, vb, adj, cur, nxt, s);
+                st = axis_op(P, W, a, vb, adj, cur, nxt, s);
                 if (st != JT_OK) return st;
                 cur = nxt;
                 which ^= 1;
             }
-            k_add<<<grid_for(ntot), 256, 0, s>>>(P->T2, cur, ntot);
+            k_add<<<grid_for(ntot), 256, 0, s>>>(W.T2, cur, ntot);
             if (cudaGetLastError() != cudaSuccess) return JT_ECUDA;
         }
-        if (cudaMemcpyAsync(dst, P->T2, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(dst, W.T2, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return JT_ECUDA;
     }
     return JT_OK;
+}
+
+}  // namespace
+
+jt_status plain_apply(PlainPlan* P, const double* in, double* out, int64_t nrhs, bool fwd, cudaStream_t s) {
+    if (!P) return JT_EINVAL;
+    const PlainScratch W{P->X, P->Z, P->T1, P->T2};
+    return plain_apply_bufs(P, W, in, out, nrhs, fwd, s);
+}
+
+namespace {
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Device address of the static work area on the current device.  Host code cannot use the
+// array's name as a device pointer, so the address is looked up once per device, with that
+// device current, and cached.
+jt_status static_scratch_address(void** out) {
+    static std::mutex mu;
+    static void* addr[128] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return JT_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, jt_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return JT_ECUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return JT_OK;
+}
+
+}  // namespace
+
+size_t plain_static_bytes(const PlainPlan* P) {
+    const long long ltot = P->D.L[0] * P->D.L[1] * P->D.L[2];
+    const long long ntot = P->D.n[0] * P->D.n[1] * P->D.n[2];
+    long long zmax = 0;
+    for (int a = 0; a < P->d; ++a) zmax = std::max(zmax, ntot / P->D.n[a] * P->D.L[a]);
+    return round256(sizeof(double2) * ltot) + round256(sizeof(double2) * zmax) + 2 * round256(sizeof(double) * ntot);
+}
+
+jt_status plain_apply_static(PlainPlan* P, const double* in, double* out, int64_t nrhs, bool fwd, cudaStream_t s) {
+    if (!P) return JT_EINVAL;
+    if (plain_static_bytes(P) > (size_t)JT_STATIC_SCRATCH_BYTES) return JT_EINVAL;
+    void* base = nullptr;
+    jt_status st = static_scratch_address(&base);
+    if (st != JT_OK) return st;
+    const long long ltot = P->D.L[0] * P->D.L[1] * P->D.L[2];
+    const long long ntot = P->D.n[0] * P->D.n[1] * P->D.n[2];
+    long long zmax = 0;
+    for (int a = 0; a < P->d; ++a) zmax = std::max(zmax, ntot / P->D.n[a] * P->D.L[a]);
+    unsigned char* q = static_cast<unsigned char*>(base);
+    PlainScratch W;
+    W.X = reinterpret_cast<double2*>(q);
+    q += round256(sizeof(double2) * ltot);
+    W.Z = reinterpret_cast<double2*>(q);
+    q += round256(sizeof(double2) * zmax);
+    W.T1 = reinterpret_cast<double*>(q);
+    q += round256(sizeof(double) * ntot);
+    W.T2 = reinterpret_cast<double*>(q);
+    // every buffer that must start at zero is cleared inside the apply (cudaMemsetAsync on the
+    // stream), so what an earlier call left in the area does not matter
+    return plain_apply_bufs(P, W, in, out, nrhs, fwd, s);
 }
 
 void plain_destroy(PlainPlan* P) {
