@@ -48,6 +48,27 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def captured_traffic():
+    """DRAM bytes per launch of the axis kernels from the committed ncu capture, or None when
+    the kernel sources have changed since the counters were taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "axis_kernels_2d512_fp32_traffic.txt")
+    csrc = os.path.join(ROOT, "paper_1901_07275_gb300", "csrc")
+    try:
+        fields = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        src = "".join(open(os.path.join(csrc, f)).read() for f in ("jt_warp.cuh", "jt_axis.cuh"))
+        if hashlib.sha256(src.encode()).hexdigest()[:16] != fields.get("kernel_source_sha256_16"):
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def axis_flops(n, L, r):
     """Algorithmic FP32 flops of one fibre of one axis: r (5 L log2 L + 8 n) + 55 n."""
     return r * (5 * L * math.log2(L) + 8 * n) + 55 * n
@@ -307,7 +328,9 @@ def main():
                    "l2": f"inputs {4 * nrhs * N[0] * N[1] / 2**20:.0f} MiB > L2 129 MB, no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / alu_peak, "traffic": None,
+                     "frac": achieved_tflops / alu_peak, "traffic": captured_traffic(),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "algorithmic_bytes_per_launch": bytes_step / 4,
                      "peak_note": f"FP32 CUDA-core peak {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                   f"{sm_max:.0f} MHz (sm_max from MEASURED_PEAKS: {peak_src})",
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
