@@ -109,6 +109,36 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
         for (int64_t j = 0; j < n; ++j) bin_idx[fill[T.m[j]]++] = (int)j;
     }
     std::vector<int> mtab(T.m.begin(), T.m.end());
+    // bin-ordered copy of u_k for the FP32 warp kernel: [k][(s * 2 + i) * TT + t] = u_k at the
+    // i-th point of bin m = t + TT s (s <= 8, i < 2), zero where the bin has fewer points
+    std::vector<Cx<R>> ubtab;
+    std::vector<int> bjtab, ovftab;
+    if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
+        const int64_t TT = L / 16;
+        bjtab.assign((size_t)18 * TT, -1);
+        ovftab.assign((size_t)TT, 0);
+        for (int64_t s2 = 0; s2 <= 8; ++s2)
+            for (int64_t t = 0; t < TT; ++t) {
+                const int64_t m = t + TT * s2;
+                if (m > L / 2) continue;
+                for (int i = 0; i < 2; ++i)
+                    if (bin_ptr[m] + i < bin_ptr[m + 1]) bjtab[(s2 * 2 + i) * TT + t] = bin_idx[bin_ptr[m] + i];
+                if (bin_ptr[m + 1] - bin_ptr[m] > 2) ovftab[t] = 1;
+            }
+        ubtab.assign((size_t)r * 18 * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
+        for (int64_t k = 0; k < r; ++k)
+            for (int64_t s2 = 0; s2 <= 8; ++s2)
+                for (int64_t t = 0; t < TT; ++t) {
+                    const int64_t m = t + TT * s2;
+                    if (m > L / 2) continue;
+                    for (int i = 0; i < 2; ++i) {
+                        const int64_t p = bin_ptr[m] + i;
+                        if (p >= bin_ptr[m + 1]) break;
+                        const int64_t j = bin_idx[p];
+                        ubtab[(size_t)k * 18 * TT + (s2 * 2 + i) * TT + t] = utab[(size_t)k * n + j];
+                    }
+                }
+    }
     AxisDev& A = ax.dev;
     A.n = (int)n;
     A.L = (int)L;
@@ -129,6 +159,11 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     A.bin_ptr = (const int*)p;
     if ((st = upload(ax, bin_idx, &p, s)) != JT_OK) return st;
     A.bin_idx = (const int*)p;
+    if ((st = upload(ax, ubtab, &A.ubtab, s)) != JT_OK) return st;
+    if ((st = upload(ax, bjtab, &p, s)) != JT_OK) return st;
+    A.bjtab = (const int*)p;
+    if ((st = upload(ax, ovftab, &p, s)) != JT_OK) return st;
+    A.ovftab = (const int*)p;
     // keep the host vectors alive until the copies are done
     if (cudaStreamSynchronize(s) != cudaSuccess) return JT_ECUDA;
     return JT_OK;

@@ -208,6 +208,26 @@ __device__ __forceinline__ void dft_stage(Cx<Rt>* t) {
     }
 }
 
+// 16-point DFT of an input whose entries 9..15 are zero (the adjoint's bins above L/2): the
+// first radix-2 stage pairs a[r] with a[r + 8], which is zero for r >= 1.
+template <class Rt>
+__device__ __forceinline__ void dft16_low9(Cx<Rt>* a) {
+    Cx<Rt> t[16];
+    t[0] = a[0] + a[8];
+    t[1] = a[0] - a[8];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+        const int r = Bitrev<16>::rev(2 * q);  // r < 8, partner r + 8 is zero
+        t[2 * q] = a[r];
+        t[2 * q + 1] = a[r];
+    }
+    dft_stage<4, 16, Rt>(t);
+    dft_stage<8, 16, Rt>(t);
+    dft_stage<16, 16, Rt>(t);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = t[i];
+}
+
 template <int R, class Rt>
 __device__ __forceinline__ void dft(Cx<Rt>* a) {
     if constexpr (R == 1) {
@@ -261,6 +281,11 @@ struct AxisDev {
     const void* twid;    // L          Cx<R>: e^{+2 pi i s / L}
     const int* bin_ptr;  // L/2 + 2    points of bin m: bin_idx[bin_ptr[m] .. bin_ptr[m+1])
     const int* bin_idx;  // n
+    // FP32 warp kernel only: u_k in bin order, rank x 9 x 2 x T complex; entry
+    // [k][(s * 2 + i) * T + t] is u_k at the i-th point of bin m = t + T s (zero if none)
+    const void* ubtab;
+    const int* bjtab;    // [(s * 2 + i) * T + t]: the point of that slot, or -1 (same layout as ubtab)
+    const int* ovftab;   // [t]: 1 if a bin of lane t holds more than two points
 };
 
 template <int T, int G>

@@ -101,14 +101,15 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     const float2* __restrict__ utab = reinterpret_cast<const float2*>(A.utab);
     const float* __restrict__ vblk = reinterpret_cast<const float*>(A.vblk);  // [c][0..L), zero beyond n
     const float2* __restrict__ tw = reinterpret_cast<const float2*>(A.twid);
+    const float2* __restrict__ ubtab = reinterpret_cast<const float2*>(A.ubtab);
 
     // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane
     Cx<float> twA[16];
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) twA[k1] = cx(__ldg(tw + ((t * k1) & (L - 1))));
-    // Per-lane constants.  Forward: padded gather-buffer index of each owned point, two
-    // 16-bit fields a word.  Adjoint: first and one-past-last point of each owned bin.
-    constexpr int NPK = FWD ? 8 : 16;
+    // Per-lane constants.  Forward: padded gather-buffer index of each owned point, two 16-bit
+    // fields a word.  Adjoint: whether one of the lane's bins holds more than two points.
+    constexpr int NPK = FWD ? 8 : 1;
     unsigned pk[NPK];
 #pragma unroll
     for (int i = 0; i < NPK; ++i) {
@@ -121,10 +122,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             }
             pk[i] = v[0] | (v[1] << 16);
         } else {
-            const int m = t + T * i;
-            unsigned v = 0;
-            if (m <= L / 2) v = (unsigned)__ldg(A.bin_ptr + m) | ((unsigned)__ldg(A.bin_ptr + m + 1) << 16);
-            pk[i] = v;
+            pk[i] = (unsigned)__ldg(A.ovftab + t);
         }
     }
     const bool sorted = A.sorted != 0;
@@ -251,6 +249,16 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         }
         __syncthreads();  // results read before the rank loop reuses the exchange region
 
+        // adjoint: g at the first two points of each owned bin (s <= 8), zero where there is none
+        float gb[FWD ? 1 : 18];
+        if constexpr (!FWD) {
+#pragma unroll
+            for (int q = 0; q < 18; ++q) {
+                const int j = __ldg(A.bjtab + q * T + t);
+                gb[q] = (j >= 0) ? aux[S::apad(j)] : 0.0f;
+            }
+        }
+
         for (int k = 0; k < rank; ++k) {
             Cx<float> x[16];
             if constexpr (FWD) {
@@ -261,41 +269,44 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     x[s] = Cx<float>{v.x * val[s], v.y * val[s]};
                 }
             } else {
-                // z[m] = sum_{j : m_j = m} u_k[j] g_j, only m <= L/2 can be reached; with the
-                // points in bin order (always so for Gauss--Jacobi nodes) point p of a bin is j = p
-                const float2* uk = utab + (size_t)k * n;
+                // z[m] = sum_{j : m_j = m} u_k[j] g_j for the owned bins m = t + T s; only
+                // m <= L/2 (s <= 8) can hold points.  The first two points of every bin come
+                // from the bin-ordered tables (u_k contiguous across lanes, g in registers);
+                // lanes with a larger bin add the remaining points from the CSR lists.
+                const float2* ubk = ubtab + (size_t)k * (18 * T);
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
-                    const int p1 = (int)(pk[s] & 0xffffu), p2 = (int)(pk[s] >> 16);
                     Cx<float> z{0.0f, 0.0f};
-                    // bins hold about two points: the first two are loaded without a loop so
-                    // that every lane issues all its loads at once; larger bins finish below
-                    const int j0 = sorted ? p1 : __ldg(A.bin_idx + min(p1, n - 1));
-                    const int j1 = sorted ? p1 + 1 : __ldg(A.bin_idx + min(p1 + 1, n - 1));
-                    if (p1 < p2) {
-                        float2 u = __ldg(uk + j0);
-                        float g = aux[S::apad(j0)];
-                        z.re = u.x * g;
-                        z.im = u.y * g;
-                    }
-                    if (p1 + 1 < p2) {
-                        float2 u = __ldg(uk + j1);
-                        float g = aux[S::apad(j1)];
-                        z.re = fmaf(u.x, g, z.re);
-                        z.im = fmaf(u.y, g, z.im);
-                    }
-                    for (int p = p1 + 2; p < p2; ++p) {
-                        int j = sorted ? p : __ldg(A.bin_idx + p);
-                        float2 u = __ldg(uk + j);
-                        float g = aux[S::apad(j)];
-                        z.re = fmaf(u.x, g, z.re);
-                        z.im = fmaf(u.y, g, z.im);
+                    if (s <= 8) {
+                        const float2 u0 = __ldg(ubk + (2 * s) * T + t);
+                        const float2 u1 = __ldg(ubk + (2 * s + 1) * T + t);
+                        z.re = fmaf(u1.x, gb[2 * s + 1], u0.x * gb[2 * s]);
+                        z.im = fmaf(u1.y, gb[2 * s + 1], u0.y * gb[2 * s]);
                     }
                     x[s] = z;
                 }
+                if (pk[0]) {
+                    const float2* uk = utab + (size_t)k * n;
+#pragma unroll
+                    for (int s = 0; s <= 8; ++s) {
+                        const int m = t + T * s;
+                        if (m > L / 2) continue;
+                        const int p2 = __ldg(A.bin_ptr + m + 1);
+                        for (int p = __ldg(A.bin_ptr + m) + 2; p < p2; ++p) {
+                            const int j = sorted ? p : __ldg(A.bin_idx + p);
+                            const float2 u = __ldg(uk + j);
+                            const float g = aux[S::apad(j)];
+                            x[s].re = fmaf(u.x, g, x[s].re);
+                            x[s].im = fmaf(u.y, g, x[s].im);
+                        }
+                    }
+                }
             }
             // step A: 16-point DFT over s, then the per-lane twiddles
-            dft<16, float>(x);
+            if constexpr (FWD)
+                dft<16, float>(x);
+            else
+                dft16_low9<float>(x);
 #pragma unroll
             for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], twA[k1]);
             // exchange: buf[k1][t]
