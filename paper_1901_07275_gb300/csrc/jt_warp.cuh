@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             float part[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) part[i] = 0.0f;
+#pragma unroll 4
             for (int c = 0; c < nu0; ++c) {
                 float vj[JPT];
 #pragma unroll
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 float part[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) part[i] = 0.0f;
+#pragma unroll
                 for (int j = lane; j < L; j += 32) {
                     const float v = __ldg(vblk + (size_t)c * L + j);
 #pragma unroll
