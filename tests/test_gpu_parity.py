@@ -220,3 +220,63 @@ def test_autograd_gradient_matches_dense_transpose_and_finite_differences(torch_
             lm = float(((jacobi_fn(a_t - dt, T) - y_t) ** 2).double().sum())
             fd = (lp - lm) / 2
             assert abs(fd - float((grad * d).sum())) < 1e-4 * (abs(lp) + abs(lm))
+
+
+# ----------------------------------------------------------- full-size cases
+def test_2d_nonuniform_1024_full(torch_dev):
+    """2-D nonuniform 1024 x 1024 (t_x, t_y i.i.d. U(0, pi), sorted, a = b = 0.25): forward
+    and adjoint against the oracle's dense J on every output, FP32."""
+    torch, dev = torch_dev
+    w = syn.workload("2d-nonuniform-1024")
+    T = make(tuple(w["n"]), w["ab"], "fp32", points=w["points"])
+    M = mats_for(w["n"], w["ab"], w["points"])
+    x = to_dev(torch, dev, w["alpha"], "fp32")
+    assert rel(T.forward(x).cpu().numpy(), oracle.forward(w["alpha"], M)) < TOL["fp32"]
+    assert rel(T.adjoint(x).cpu().numpy(), oracle.adjoint(w["alpha"], M)) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec,n", [("fp32", 16384), ("split", 8192), ("fp32", 12000), ("split", 5000)])
+def test_1d_long_sampled(torch_dev, prec, n):
+    """Longest supported axes (n = 16384 FP32, 8192 split) and ragged lengths: 96 seeded
+    output rows against the oracle's rows of W J; the adjoint through <W J^T g, e_i>."""
+    torch, dev = torch_dev
+    ab = [(0.1, -0.3)]
+    alpha = syn.normal(300 + n, 0, (2, n))
+    T = make((n,), ab, prec)
+    f = T.forward(to_dev(torch, dev, alpha, prec)).double().cpu().numpy()
+    rows = np.unique(syn.integers(301 + n, 3, 96, 0, n))
+    rows = np.union1d(rows, [0, 1, n - 2, n - 1])
+    Q = oracle.uniform_rows(ab[0][0], ab[0][1], n, rows)
+    assert rel(f[:, rows], alpha @ Q.T) < TOL[prec]
+    # adjoint: (W J)^T g restricted to the sampled rows of g equals Q^T g_rows
+    g = np.zeros((1, n))
+    g[0, rows] = syn.normal(302 + n, 0, (rows.size,))
+    a = T.adjoint(to_dev(torch, dev, g, prec)).double().cpu().numpy()
+    assert rel(a, g[:, rows] @ Q) < TOL[prec]
+
+
+def test_2d_1024_uniform_sampled(torch_dev):
+    """2-D 1024 x 1024 uniform, random (a, b) per axis: 4096 sampled outputs."""
+    torch, dev = torch_dev
+    n = (1024, 1024)
+    ab = [(0.21, -0.37), (-0.44, 0.05)]
+    alpha = syn.normal(1024, 0, n)
+    T = make(n, ab, "fp32")
+    f = T.forward(to_dev(torch, dev, alpha, "fp32")).double().cpu().numpy()
+    idx = np.stack([syn.integers(1025, 3 + 10 * a, 4096, 0, 1024) for a in range(2)], axis=1)
+    rows = [oracle.uniform_rows(a, b, 1024, idx[:, k]) for k, (a, b) in enumerate(ab)]
+    ref = oracle.forward_sampled(alpha, rows, idx)
+    assert rel(f[idx[:, 0], idx[:, 1]], ref) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 17])
+def test_batched_right_hand_sides_match_one_at_a_time(torch_dev, nrhs):
+    """A batch of right-hand sides gives each one's transform (ragged batch sizes)."""
+    torch, dev = torch_dev
+    n = (200, 130)
+    ab = [(0.1, 0.2), (-0.3, 0.4)]
+    T = make(n, ab, "fp32")
+    x = to_dev(torch, dev, syn.normal(5 + nrhs, 0, (nrhs,) + n), "fp32")
+    y = T.forward(x)
+    for r in range(nrhs):
+        assert torch.equal(y[r], T.forward(x[r].contiguous()))
