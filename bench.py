@@ -238,6 +238,47 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- GPU arm
+def other_configs(dev, stream):
+    """Throughput of the FP32 kernels on the other workloads (forward + inverse/adjoint per
+    step, CUDA events, 2 warm-up and 3 timed steps each)."""
+    import torch
+
+    from paper_1901_07275_gb300 import Transform
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    out = {}
+    cases = [
+        ("1d-1024 x 8192 rhs", "1d-1024", 8192),
+        ("3d-256", "3d-256", 1),
+        ("2d-nonuniform-1024 x 16 rhs (forward + adjoint)", "2d-nonuniform-1024", 16),
+    ]
+    for label, name, nr in cases:
+        w = syn.workload(name, nrhs=1)
+        T = Transform(w["n"], [p[0] for p in w["ab"]], [p[1] for p in w["ab"]], points=w["points"], eps=1e-7)
+        x = torch.tensor(w["alpha"], dtype=torch.float32, device=dev).expand((nr,) + tuple(w["n"])).contiguous()
+        f = torch.empty_like(x)
+        y = torch.empty_like(x)
+        back = T.inverse if T.uniform else T.adjoint
+        for _ in range(2):
+            T.forward(x, out=f)
+            back(f, out=y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            T.forward(x, out=f)
+            back(f, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        coeffs = 2 * x.numel()
+        out[label] = {"coeffs_per_s": coeffs / (ms * 1e-3), "ms_per_step": ms, "ranks": T.ranks,
+                      "fft_len": T.fft_lens}
+        T.close()
+        del x, f, y
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,6 +462,8 @@ def main():
                               "speedup_fp32_over_plain": value / world / plain_v,
                               "speedup_split_over_plain": split_v / plain_v}
         Tp.close()
+
+        line["other_configs"] = other_configs(dev, stream)
 
         if world == 1:
             line["cpu_baseline"] = oracle_throughput(nrhs)

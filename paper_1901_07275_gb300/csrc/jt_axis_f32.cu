@@ -1,5 +1,5 @@
-// FP32 instances of the fused axis kernels: the warp-level kernel for L = 16 .. 512,
-// the general Stockham kernel otherwise (L = 1 .. 8 and 1024 .. 16384).
+// FP32 instances of the fused axis kernels: the four-step kernel for L = 16 .. 4096, the
+// general Stockham kernel otherwise (L = 1 .. 8 and 8192 .. 16384).
 #include "jt_launch_impl.cuh"
 #include "jt_warp.cuh"
 
@@ -43,14 +43,14 @@ static cudaError_t warp_dispatch(int log2L, const dev::AxisDev& A, bool fwd, con
         return strided ? launch_warp<LOG2L, false, true>(A, in, out, nfib, inner, s)
                        : launch_warp<LOG2L, false, false>(A, in, out, nfib, inner, s);
     }
-    if constexpr (LOG2L > 4) return warp_dispatch<LOG2L - 1>(log2L, A, fwd, in, out, nfib, inner, s);
+    if constexpr (LOG2L > F32_WARP_MIN_LOG2L) return warp_dispatch<LOG2L - 1>(log2L, A, fwd, in, out, nfib, inner, s);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_axis_f32(const dev::AxisDev& A, int log2L, bool fwd, const float* in, float* out,
                             long long nfib, long long inner, cudaStream_t s) {
     if (log2L < 0 || log2L > MAX_LOG2L_F32) return cudaErrorInvalidValue;
-    if (f32_warp_path(log2L)) return warp_dispatch<9>(log2L, A, fwd, in, out, nfib, inner, s);
+    if (f32_warp_path(log2L)) return warp_dispatch<F32_WARP_MAX_LOG2L>(log2L, A, fwd, in, out, nfib, inner, s);
     return dispatch<float, MAX_LOG2L_F32>(log2L, A, fwd, in, out, nfib, inner, s);
 }
 

@@ -17,8 +17,10 @@ cudaError_t launch_axis_dw(const dev::AxisDev& A, int log2L, bool fwd, const dou
 constexpr int MAX_LOG2L_F32 = 14;
 constexpr int MAX_LOG2L_DW = 13;
 
-// FP32 lengths 16..512 use the warp-level kernel (jt_warp.cuh), whose dense-block table rows
+// FP32 lengths 16..4096 use the four-step kernel (jt_warp.cuh), whose dense-block table rows
 // are padded with zeros to length L: vblk[c * L + j] = sqrt(w_j) P~_c(t_j) for j < n.
-constexpr bool f32_warp_path(int log2L) { return log2L >= 4 && log2L <= 9; }
+constexpr int F32_WARP_MIN_LOG2L = 4;
+constexpr int F32_WARP_MAX_LOG2L = 12;
+constexpr bool f32_warp_path(int log2L) { return log2L >= F32_WARP_MIN_LOG2L && log2L <= F32_WARP_MAX_LOG2L; }
 
 }  // namespace jt

@@ -1,5 +1,6 @@
-// Warp-level fused axis kernel for FFT lengths L = 16 T, T in {1, 2, 4, 8, 16, 32}
-// (L = 16 .. 512), FP32.  One group of T lanes owns one fibre; a warp holds 32 / T fibres.
+// Fused axis kernel for FFT lengths L = 16 T, T in {1, 2, .., 256} (L = 16 .. 4096), FP32.
+// One group of T lanes owns one fibre: a warp holds 32 / T fibres for T <= 32, a fibre
+// spans T / 32 warps for T >= 64.
 //
 // The length-L inverse DFT (sign +) is split in four steps, L = 16 x T: with input index
 // p = t + T s (lane t < T holds s = 0..15 in registers) and output index m = k1 + 16 k2,
@@ -9,7 +10,8 @@
 // through shared memory regroups the values by k1, and step B finishes the T-point DFTs:
 // for T <= 16 each lane owns 16/T whole problems; for T = 32 each problem is split over a
 // lane pair (16-point DFTs on the even and odd lanes, then one radix-2 stage through a
-// shuffle).  The forward keeps only the outputs m <= L/2 that the gather can use.
+// shuffle); for T >= 64 over R = T/16 lanes (16-point DFTs, a second exchange, R-point DFTs).
+// The forward keeps only the outputs m <= L/2 that the gather can use.
 //
 // Fibres of a strided axis are staged through a shared-memory tile so that every global
 // load and store touches whole 32-byte sectors.
@@ -29,18 +31,21 @@ template <int LOG2L>
 struct WShape {
     static constexpr int L = 1 << LOG2L;
     static constexpr int E = 16;
-    static constexpr int T = L / E;          // lanes per fibre
-    static constexpr int FPW = 32 / T;       // fibres per warp
+    static constexpr int T = L / E;          // lanes per fibre (1 .. 256)
     static constexpr int WARPS = 8;
     static constexpr int THREADS = 32 * WARPS;
-    static constexpr int FT = WARPS * FPW;   // fibres per CTA iteration
+    static constexpr int FT = THREADS / T;   // fibres per CTA iteration
+    static constexpr int R = (T >= 64) ? T / 16 : 1;  // T >= 64: lanes per step-B problem
+    static constexpr int QP = 16 / R;                 // T >= 64: k2' values a lane finishes
     // Exchange rows are padded so that the 64-bit accesses of a half-warp never share a bank:
-    // row k1 starts at k1 * XROW float2; T = 32 reads (k1 = t/2, column 2q + h) need an even
-    // pad, T <= 16 reads (k1 = t) an odd one.
-    static constexpr int XROW = (T == 32) ? T + 2 : T + 1;
+    // row k1 starts at k1 * XROW float2.  T = 32 reads (k1 = t/2, column 2q + h) need an even
+    // pad, T <= 16 reads (k1 = t) an odd one, T >= 64 reads (k1 = t/R, column R q + h) R.
+    static constexpr int XROW = (T == 32) ? T + 2 : (T >= 64) ? T + R : T + 1;
     static constexpr int XBUF = 16 * XROW;   // exchange buffer per fibre (float2)
+    static constexpr int X2BUF = (T >= 64) ? 16 * 16 * R : 0;      // second exchange (T >= 64)
     static constexpr int YBUF = L / 2 + 1 + ((L / 2) >> 4) + 1;  // gather buffer (float2)
-    static constexpr int BUF = (XBUF > YBUF ? XBUF : YBUF);
+    static constexpr int BUF0 = (XBUF > YBUF ? XBUF : YBUF);
+    static constexpr int BUF = (BUF0 > X2BUF ? BUF0 : X2BUF);
     static constexpr int AUX = L + L / 32 + 1;                  // per fibre: alpha_V / g (floats)
     // staging tile rows: consecutive threads cover FT fibres x (32 / FT) rows
     static constexpr int TROW = L + ((FT >= 32) ? 1 : 32 / FT);
@@ -49,7 +54,24 @@ struct WShape {
     // adjoint copy of g: lanes read points ~2t (stride 2) in the scatter and consecutive
     // points in the dense block; j + j/32 keeps both patterns free of bank conflicts
     static __host__ __device__ constexpr int apad(int j) { return j + (j >> 5); }
+    // second exchange (T >= 64): B_h[k2'] of problem k1, rotated within its R-group so that the
+    // reads of a half-warp (different k1, h, rows k2' = h QP + i) hit different banks
+    static __host__ __device__ constexpr int x2idx(int k1, int k2, int h) {
+        return k2 * (16 * R) + k1 * R + ((h + k2 / QP) % R);
+    }
 };
+
+// Synchronise the T lanes of one fibre group (a warp or less, one CTA, or a named barrier).
+template <int T, int FT>
+__device__ __forceinline__ void gsync(int fl) {
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else if constexpr (FT == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(fl + 1), "r"(T) : "memory");
+    }
+}
 
 template <int LOG2L>
 constexpr size_t warp_smem_bytes(bool strided) {
@@ -74,6 +96,10 @@ struct Own {
         if constexpr (T == 32) {
             const int k1 = t >> 1, h = t & 1;
             return k1 + 16 * (h * 8 + (o & 7)) + (o >> 3) * (S::L / 2);  // o < 8: g = 0, o >= 8: g = 1
+        } else if constexpr (T >= 64) {
+            const int k1 = t / S::R, h = t % S::R;
+            const int i = o / S::R, g = o % S::R;
+            return k1 + 16 * (h * S::QP + i + 16 * g);
         } else {
             constexpr int P = 16 / T;  // problems per lane
             const int q = o / T, k2 = o % T;
@@ -90,8 +116,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     constexpr int L = S::L, T = S::T, FT = S::FT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int fl = warp * S::FPW + lane / T;  // fibre slot in the CTA tile
-    const int t = lane % T;
+    const int fl = threadIdx.x / T;  // fibre slot in the CTA tile
+    const int t = threadIdx.x % T;
     float2* buf = reinterpret_cast<float2*>(smem_raw) + (size_t)fl * S::BUF;
     float* aux = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)fl * S::AUX;
     float* tile = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)FT * S::AUX;
@@ -312,10 +338,10 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
 #pragma unroll
             for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], twA[k1]);
             // exchange: buf[k1][t]
-            __syncwarp();
+            gsync<T, FT>(fl);
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) buf[k1 * S::XROW + t] = f2(x[k1]);
-            __syncwarp();
+            gsync<T, FT>(fl);
             Cx<float> y[16];  // step-B outputs in Own<> order
             if constexpr (T == 32) {
                 const int k1 = t >> 1, h = t & 1;
@@ -352,6 +378,31 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     Cx<float> d = own - recv;
                     y[8 + i] = h ? Cx<float>{-d.re, -d.im} : d;
                 }
+            } else if constexpr (T >= 64) {
+                // problem k1 is split over R lanes h: a 16-point DFT over q of X1[R q + h][k1],
+                // the twiddle w_T^{h k2'}, a second exchange, then R-point DFTs over h
+                constexpr int R = S::R, QP = S::QP;
+                const int k1 = t / R, h = t % R;
+                Cx<float> a[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) a[q] = cx(buf[k1 * S::XROW + R * q + h]);
+                dft<16, float>(a);
+#pragma unroll
+                for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], cx(__ldg(tw + ((16 * h * k2) & (L - 1)))));
+                gsync<T, FT>(fl);
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) buf[S::x2idx(k1, k2, h)] = f2(a[k2]);
+                gsync<T, FT>(fl);
+#pragma unroll
+                for (int i = 0; i < QP; ++i) {
+                    const int k2 = h * QP + i;
+                    Cx<float> b[R];
+#pragma unroll
+                    for (int hh = 0; hh < R; ++hh) b[hh] = cx(buf[S::x2idx(k1, k2, hh)]);
+                    dft<R, float>(b);
+#pragma unroll
+                    for (int g2 = 0; g2 < R; ++g2) y[i * R + g2] = b[g2];
+                }
             } else {
                 constexpr int P = 16 / T;
 #pragma unroll
@@ -367,13 +418,13 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             }
             if constexpr (FWD) {
                 // Y[m] for m <= L/2 into the gather buffer, then acc_j += Re(u_k[j] Y[m_j])
-                __syncwarp();
+                gsync<T, FT>(fl);
 #pragma unroll
                 for (int o = 0; o < 16; ++o) {
                     int m = Own<LOG2L, FWD>::idx(t, o);
                     if (m <= L / 2) buf[S::ypad(m)] = f2(y[o]);
                 }
-                __syncwarp();
+                gsync<T, FT>(fl);
                 const float2* uk = utab + (size_t)k * n;
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {

@@ -235,7 +235,11 @@ def test_2d_nonuniform_1024_full(torch_dev):
     assert rel(T.adjoint(x).cpu().numpy(), oracle.adjoint(w["alpha"], M)) < TOL["fp32"]
 
 
-@pytest.mark.parametrize("prec,n", [("fp32", 16384), ("split", 8192), ("fp32", 12000), ("split", 5000)])
+@pytest.mark.parametrize(
+    "prec,n",
+    [("fp32", 16384), ("split", 8192), ("fp32", 12000), ("split", 5000), ("fp32", 2048), ("fp32", 3000), ("fp32", 4096),
+     ("fp32", 1500)],
+)
 def test_1d_long_sampled(torch_dev, prec, n):
     """Longest supported axes (n = 16384 FP32, 8192 split) and ragged lengths: 96 seeded
     output rows against the oracle's rows of W J; the adjoint through <W J^T g, e_i>."""
@@ -280,3 +284,24 @@ def test_batched_right_hand_sides_match_one_at_a_time(torch_dev, nrhs):
     y = T.forward(x)
     for r in range(nrhs):
         assert torch.equal(y[r], T.forward(x[r].contiguous()))
+
+
+@pytest.mark.parametrize("n", [(2048, 40), (36, 4096), (1200, 24)])
+def test_2d_long_axes_sampled(torch_dev, n):
+    """Long axes on either side of a 2-D array (contiguous and strided sweeps of the four-step
+    kernel at L = 2048 and 4096), forward against 2048 sampled outputs."""
+    torch, dev = torch_dev
+    ab = [(0.2, -0.1), (-0.35, 0.45)]
+    alpha = syn.normal(2048 + n[0], 0, n)
+    T = make(n, ab, "fp32")
+    f = T.forward(to_dev(torch, dev, alpha, "fp32")).double().cpu().numpy()
+    idx = np.stack([syn.integers(2049 + n[0], 3 + 10 * a, 2048, 0, n[a]) for a in range(2)], axis=1)
+    rows = [oracle.uniform_rows(a, b, n[k], idx[:, k]) for k, (a, b) in enumerate(ab)]
+    ref = oracle.forward_sampled(alpha, rows, idx)
+    assert rel(f[idx[:, 0], idx[:, 1]], ref) < TOL["fp32"]
+    g = T.adjoint(to_dev(torch, dev, alpha, "fp32")).double().cpu().numpy()
+    # adjoint = transpose: <A x, y> = <x, A^T y> against the forward just checked
+    y = syn.normal(2050 + n[0], 0, n)
+    lhs = float((T.forward(to_dev(torch, dev, y, "fp32")).double().cpu().numpy() * alpha).sum())
+    rhs = float((g * y).sum())
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(alpha) * np.linalg.norm(y)
