@@ -152,14 +152,21 @@ def barrier(world):
 
 
 def max_over_ranks(world, v):
+    """Largest value over all ranks (the timed region of the slowest replica)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(world, coeffs_per_step_per_rank, steps, total_ms):
+    """Whole-job throughput of `world` replicas: all ranks' work over the slowest rank's time."""
+    return world * coeffs_per_step_per_rank * steps / (total_ms * 1e-3)
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -347,7 +354,7 @@ def main():
     clocks = clk.summary()
 
     coeffs_per_step = 2 * nrhs * N[0] * N[1]
-    value = world * coeffs_per_step * args.steps / (total_ms * 1e-3)
+    value = aggregate(world, coeffs_per_step, args.steps, total_ms)
 
     # roofline of the fused axis kernel: 4 launches per step (2 axes x forward/inverse)
     flops_step = 2 * sum(nrhs * (N[0] * N[1] // N[a]) * axis_flops(N[a], Ls[a], ranks[a]) for a in range(2))
