@@ -48,7 +48,7 @@ static const double NEAR_END = 0.35;
 bool valid_parameter(double v) { return std::isfinite(v) && v > -1.0 && v < 1.0; }
 
 // ------------------------------------------------------------ double-word numbers
-namespace {  // anon
+namespace {
 
 struct DD {
     double hi, lo;
@@ -216,30 +216,46 @@ void pn_block(const Coefs& C, int64_t n, const R* x, int nb, R* p, double* dp, R
     }
 }
 
-template <class R>
-void newton_block(const Coefs& C, int64_t n, double maxstep, double* t, double* omega, int nb) {
+// Newton in t for a block of zeros of p_n(cos t).  The iteration runs in FP64; points near
+// the ends (`dw`) then take two more steps with double-word evaluations, the second of
+// which also gives the Christoffel number.  FP64 alone converges to within the accuracy of
+// its own evaluation, so those two steps are enough to reach a root of the exact polynomial.
+void newton_block(const Coefs& C, int64_t n, double maxstep, double* t, double* omega, int nb, bool dw) {
     std::vector<int> act(nb);
     std::iota(act.begin(), act.end(), 0);
-    std::vector<R> x(nb), p(nb), s(nb);
-    std::vector<double> dp(nb);
+    std::vector<double> x(nb), p(nb), s(nb), dp(nb);
+    const double tol = dw ? 1e-13 : 2e-16;
     for (int it = 0; it < 40 && !act.empty(); ++it) {
         int na = (int)act.size();
         for (int q = 0; q < na; ++q) make_x(t[act[q]], x[q]);
-        pn_block<R>(C, n, x.data(), na, p.data(), dp.data(), s.data());
+        pn_block<double>(C, n, x.data(), na, p.data(), dp.data(), s.data());
         std::vector<int> still;
         for (int q = 0; q < na; ++q) {
             int k = act[q];
-            double dt = todouble(p[q]) / (std::sin(t[k]) * dp[q]);
+            double dt = p[q] / (std::sin(t[k]) * dp[q]);
             if (!std::isfinite(dt)) dt = 0.0;
             dt = std::max(-maxstep, std::min(maxstep, dt));
             t[k] += dt;
-            if (std::abs(dt) > 2e-16 * std::min(t[k], PI - t[k])) still.push_back(k);
+            if (std::abs(dt) > tol * std::min(t[k], PI - t[k])) still.push_back(k);
         }
         act.swap(still);
     }
-    for (int k = 0; k < nb; ++k) make_x(t[k], x[k]);
-    pn_block<R>(C, n, x.data(), nb, p.data(), dp.data(), s.data());
-    for (int k = 0; k < nb; ++k) omega[k] = 1.0 / todouble(s[k]);
+    if (!dw) {
+        for (int k = 0; k < nb; ++k) make_x(t[k], x[k]);
+        pn_block<double>(C, n, x.data(), nb, p.data(), dp.data(), s.data());
+        for (int k = 0; k < nb; ++k) omega[k] = 1.0 / s[k];
+        return;
+    }
+    std::vector<DD> xd(nb), pd(nb), sd(nb);
+    for (int step = 0; step < 2; ++step) {
+        for (int k = 0; k < nb; ++k) make_x(t[k], xd[k]);
+        pn_block<DD>(C, n, xd.data(), nb, pd.data(), dp.data(), sd.data());
+        for (int k = 0; k < nb; ++k) {
+            double dt = todouble(pd[k]) / (std::sin(t[k]) * dp[k]);
+            if (step == 0 && std::isfinite(dt) && std::abs(dt) < maxstep) t[k] += dt;
+            if (step == 1) omega[k] = 1.0 / todouble(sd[k]);
+        }
+    }
 }
 
 // Serial FP64 evaluation for the bracketing fallback.
@@ -296,10 +312,7 @@ bool nodes_newton(const Coefs& C, double a, double b, int64_t n, std::vector<dou
         int64_t lo = ib * BS, hi = std::min<int64_t>(n, lo + BS);
         bool nearb = false;
         for (int64_t k = lo; k < hi; ++k) nearb = nearb || near_end(t[k]);
-        if (nearb)
-            newton_block<DD>(C, n, maxstep, &t[lo], &omega[lo], (int)(hi - lo));
-        else
-            newton_block<double>(C, n, maxstep, &t[lo], &omega[lo], (int)(hi - lo));
+        newton_block(C, n, maxstep, &t[lo], &omega[lo], (int)(hi - lo), nearb);
     });
     return true;
 }
@@ -349,10 +362,7 @@ bool nodes_scan(const Coefs& C, double a, double b, int64_t n, std::vector<doubl
     omega.assign(n, 0.0);
     const double maxstep = 1e-3 * h;
     for (int64_t k = 0; k < n; ++k) {
-        if (near_end(t[k]))
-            newton_block<DD>(C, n, maxstep, &t[k], &omega[k], 1);
-        else
-            newton_block<double>(C, n, maxstep, &t[k], &omega[k], 1);
+        newton_block(C, n, maxstep, &t[k], &omega[k], 1, near_end(t[k]));
     }
     return true;
 }
