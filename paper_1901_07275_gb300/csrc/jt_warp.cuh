@@ -243,13 +243,14 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             // alpha_c(fibre) = sum_j vblk[c][j] g_j: warp w takes (fibre chunk, degree) items,
             // lanes split the points, partials for 8 fibres at a time, then a warp sum
             constexpr int NCH = (FT + 7) / 8;
-            for (int item = warp; item < NCH * nu0; item += S::WARPS) {
-                const int ch = item / nu0, c = item % nu0;
+            constexpr int HALF = L / 2;  // items cover half of the points each, for balance
+            for (int item = warp; item < 2 * NCH * nu0; item += S::WARPS) {
+                const int half = item & 1, ch = (item >> 1) / nu0, c = (item >> 1) % nu0;
                 float part[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) part[i] = 0.0f;
 #pragma unroll
-                for (int j = lane; j < L; j += 32) {
+                for (int j = half * HALF + lane; j < (half + 1) * HALF; j += 32) {
                     const float v = __ldg(vblk + (size_t)c * L + j);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -265,14 +266,14 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 if (lane == 0) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
-                        if (ch * 8 + i < FT) vres[(ch * 8 + i) * 32 + c] = part[i];
+                        if (ch * 8 + i < FT) vres[(half * FT + ch * 8 + i) * 32 + c] = part[i];
                 }
             }
             __syncthreads();
 #pragma unroll
             for (int o = 0; o < 16; ++o) {
                 const int nu = Own<LOG2L, FWD>::idx(t, o);
-                acc[o] = (nu < nu0) ? vres[fl * 32 + nu] : 0.0f;
+                acc[o] = (nu < nu0) ? vres[fl * 32 + nu] + vres[(FT + fl) * 32 + nu] : 0.0f;
             }
         }
         __syncthreads();  // results read before the rank loop reuses the exchange region
@@ -341,6 +342,13 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             gsync<T, FT>(fl);
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) buf[k1 * S::XROW + t] = f2(x[k1]);
+            // adjoint: the v_k values the end of this rank term needs, fetched while step B runs
+            float2 post[FWD ? 1 : 16];
+            if constexpr (!FWD) {
+                const float2* vk = vtab + (size_t)k * L;
+#pragma unroll
+                for (int o = 0; o < 16; ++o) post[o] = __ldg(vk + Own<LOG2L, FWD>::idx(t, o));
+            }
             gsync<T, FT>(fl);
             Cx<float> y[16];  // step-B outputs in Own<> order
             if constexpr (T == 32) {
@@ -425,23 +433,20 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     if (m <= L / 2) buf[S::ypad(m)] = f2(y[o]);
                 }
                 gsync<T, FT>(fl);
-                const float2* uk = utab + (size_t)k * n;
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     int j = t + T * e;
                     if (j < n) {
                         const unsigned ym = (e & 1) ? (pk[e >> 1] >> 16) : (pk[e >> 1] & 0xffffu);
                         float2 yy = buf[ym];
-                        float2 u = __ldg(uk + j);
+                        const float2 u = __ldg(utab + (size_t)k * n + j);
                         acc[e] = fmaf(u.x, yy.x, fmaf(-u.y, yy.y, acc[e]));
                     }
                 }
             } else {
-                const float2* vk = vtab + (size_t)k * L;
 #pragma unroll
                 for (int o = 0; o < 16; ++o) {
-                    int nu = Own<LOG2L, FWD>::idx(t, o);
-                    float2 v = __ldg(vk + nu);
+                    const float2 v = post[o];
                     acc[o] = fmaf(v.x, y[o].re, fmaf(-v.y, y[o].im, acc[o]));
                 }
             }
