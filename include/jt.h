@@ -139,6 +139,31 @@ jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_le
 /* Release a plan and its device tables.  NULL is accepted. */
 void jt_destroy(jt_plan* plan);
 
+/* ------------------------------------------------------------------------------------
+ * Batches: many transforms of one precision (JT_FP32 or JT_SPLIT), each with its own plan
+ * (any d, n, a, b, points) and number of right-hand sides, executed together.  The axis
+ * sweeps are grouped by stage (the s-th sweep of every transform, Sec. 3.2-3.3) and, within
+ * a stage, by FFT length and stride kind; FP32 sweeps of length 16..4096 of one group run as
+ * a single kernel launch over all their fibres, other sweeps one launch each.
+ * ------------------------------------------------------------------------------------ */
+typedef struct jt_batch jt_batch;
+
+/* Build the schedule of a batch of `count` plans (not owned; they must outlive the batch)
+ * with nrhs[i] >= 1 right-hand sides each; uploads the job tables on `stream` and
+ * synchronises it.  JT_EINVAL for mixed precisions or bad arguments, JT_ENOTSUP for
+ * JT_FP64_PLAIN plans. */
+jt_status jt_batch_create(jt_batch** out, int count, jt_plan* const* plans, const int64_t* nrhs,
+                          jt_stream_t stream);
+
+/* Forward / adjoint transform of every member: in[i], out[i] are device arrays of member i
+ * (layout and aliasing rules of jt_forward).  Host arrays `in`, `out` hold count pointers.
+ * Only kernel launches are issued (no allocation, copy or synchronisation). */
+jt_status jt_batch_forward(jt_batch* batch, const void* const* in, void* const* out, jt_stream_t stream);
+jt_status jt_batch_adjoint(jt_batch* batch, const void* const* in, void* const* out, jt_stream_t stream);
+
+/* Release a batch (not its plans).  NULL is accepted. */
+void jt_batch_destroy(jt_batch* batch);
+
 /* Static string naming a status code. */
 const char* jt_status_string(jt_status s);
 

@@ -5,6 +5,6 @@ through libjt, a C-ABI library of hand-written sm_103a kernels (``include/jt.h``
 ``binding`` is the same ABI with its C names; ``build`` compiles the library in-tree.
 """
 
-from .transform import Transform, jacobi_fn  # noqa: F401
+from .transform import Batch, Transform, jacobi_fn  # noqa: F401
 
-__all__ = ["Transform", "jacobi_fn"]
+__all__ = ["Batch", "Transform", "jacobi_fn"]

@@ -29,6 +29,10 @@ EXPORTS = (
     "jt_forward_plain_noalloc",
     "jt_plan_info",
     "jt_destroy",
+    "jt_batch_create",
+    "jt_batch_forward",
+    "jt_batch_adjoint",
+    "jt_batch_destroy",
     "jt_status_string",
     "jt_axis_tables_create",
     "jt_axis_tables_info",
@@ -82,6 +86,14 @@ def lib() -> ctypes.CDLL:
     L.jt_plan_info.restype = i32
     L.jt_destroy.argtypes = [vp]
     L.jt_destroy.restype = None
+    L.jt_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64), vp]
+    L.jt_batch_create.restype = i32
+    for name in ("jt_batch_forward", "jt_batch_adjoint"):
+        f = getattr(L, name)
+        f.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        f.restype = i32
+    L.jt_batch_destroy.argtypes = [vp]
+    L.jt_batch_destroy.restype = None
     L.jt_status_string.argtypes = [i32]
     L.jt_status_string.restype = ctypes.c_char_p
     L.jt_axis_tables_create.argtypes = [ctypes.POINTER(vp), i64, dbl, dbl, vp, dbl, ctypes.POINTER(Options)]
@@ -183,6 +195,33 @@ def jt_plan_info(plan: int, axis: int, n: int | None = None):
 
 def jt_destroy(plan: int) -> None:
     lib().jt_destroy(_ptr(plan))
+
+
+def jt_batch_create(plans, nrhs, stream: int = 0) -> int:
+    count = len(plans)
+    parr = (ctypes.c_void_p * count)(*plans)
+    narr = (ctypes.c_int64 * count)(*[int(v) for v in nrhs])
+    h = ctypes.c_void_p()
+    _check(lib().jt_batch_create(ctypes.byref(h), count, parr, narr, _ptr(stream)), "jt_batch_create")
+    return h.value
+
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[int(p) for p in ptrs])
+
+
+def jt_batch_forward(batch: int, in_ptrs, out_ptrs, stream: int = 0) -> None:
+    _check(lib().jt_batch_forward(_ptr(batch), _ptr_array(in_ptrs), _ptr_array(out_ptrs), _ptr(stream)),
+           "jt_batch_forward")
+
+
+def jt_batch_adjoint(batch: int, in_ptrs, out_ptrs, stream: int = 0) -> None:
+    _check(lib().jt_batch_adjoint(_ptr(batch), _ptr_array(in_ptrs), _ptr_array(out_ptrs), _ptr(stream)),
+           "jt_batch_adjoint")
+
+
+def jt_batch_destroy(batch: int) -> None:
+    lib().jt_batch_destroy(_ptr(batch))
 
 
 # ------------------------------------------------------------ axis tables

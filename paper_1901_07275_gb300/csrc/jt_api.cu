@@ -8,6 +8,7 @@
 // array is needed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -217,7 +218,196 @@ jt_status apply(jt_plan* plan, const void* in, void* out, int64_t nrhs, bool fwd
 
 }  // namespace
 
+// A batch: the axis sweeps of several plans, grouped by stage (the s-th sweep of every
+// transform) and, inside a stage, by FFT length and stride kind.  FP32 sweeps of length
+// 16..4096 run as one launch per group (at most BATCH_MAX_JOBS jobs a launch); every other
+// sweep is launched on its own.  Nothing is allocated or copied at execution, so an execution
+// can be captured in a CUDA graph.
+struct jt_batch {
+    int count = 0;
+    int prec = JT_FP32;
+    std::vector<jt_plan*> plans;
+    std::vector<int64_t> nrhs;
+    struct Launch {
+        bool fused = false;
+        int stage = 0, log2L = 0;
+        bool strided = false;
+        // fused: device jobs [job_off, job_off + njobs), slot -> transform index
+        int job_off = 0, njobs = 0;
+        long long total_tiles = 0;
+        std::vector<int> slot_transform;
+        // single: transform index and axis
+        int transform = 0, axis = 0;
+        long long nfib = 0, inner = 1;
+    };
+    std::vector<Launch> launches;
+    jt::dev::BatchJob* d_jobs = nullptr;
+};
+
+namespace {
+
+struct SweepJob {
+    int transform, axis, stage, log2L;
+    bool strided, fused;
+    long long nfib, inner;
+};
+
+jt_status batch_run(jt_batch* b, const void* const* in, void* const* out, bool fwd, cudaStream_t s) {
+    if (!b || !in || !out) return JT_EINVAL;
+    for (int i = 0; i < b->count; ++i)
+        if (!in[i] || !out[i]) return JT_EINVAL;
+    for (const auto& L : b->launches) {
+        cudaError_t e = cudaSuccess;
+        if (L.fused) {
+            jt::dev::BatchPtrs ptrs;
+            for (size_t q = 0; q < L.slot_transform.size(); ++q) {
+                const int i = L.slot_transform[q];
+                ptrs.in[q] = (const float*)(L.stage == 0 ? in[i] : out[i]);
+                ptrs.out[q] = (float*)out[i];
+            }
+            e = jt::launch_axis_f32_batched(L.log2L, fwd, L.strided, b->d_jobs + L.job_off, L.njobs, L.total_tiles,
+                                            ptrs, s);
+        } else {
+            const jt_plan* p = b->plans[L.transform];
+            const DeviceAxis& A = p->axes[L.axis];
+            const void* src = (L.stage == 0) ? in[L.transform] : out[L.transform];
+            if (b->prec == JT_FP32)
+                e = jt::launch_axis_f32(A.dev, A.log2L, fwd, (const float*)src, (float*)out[L.transform], L.nfib,
+                                        L.inner, s);
+            else
+                e = jt::launch_axis_dw(A.dev, A.log2L, fwd, (const double*)src, (double*)out[L.transform], L.nfib,
+                                       L.inner, s);
+        }
+        if (e != cudaSuccess) return JT_ECUDA;
+    }
+    return JT_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+jt_status jt_batch_create(jt_batch** out, int count, jt_plan* const* plans, const int64_t* nrhs, jt_stream_t stream) {
+    if (!out) return JT_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !plans || !nrhs) return JT_EINVAL;
+    const int prec = plans[0] ? plans[0]->prec : -1;
+    if (prec != JT_FP32 && prec != JT_SPLIT) return (prec == JT_FP64_PLAIN) ? JT_ENOTSUP : JT_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || nrhs[i] < 1) return JT_EINVAL;
+        if (plans[i]->prec != prec) return JT_EINVAL;
+    }
+    jt_batch* b = nullptr;
+    try {
+        b = new jt_batch();
+        b->count = count;
+        b->prec = prec;
+        b->plans.assign(plans, plans + count);
+        b->nrhs.assign(nrhs, nrhs + count);
+        // sweeps of every transform, last axis first (the order of jt_forward)
+        std::vector<SweepJob> sweeps;
+        int max_stage = 0;
+        for (int i = 0; i < count; ++i) {
+            const jt_plan* p = plans[i];
+            int64_t total = nrhs[i];
+            for (int a = 0; a < p->d; ++a) total *= p->n[a];
+            for (int a = p->d - 1, st = 0; a >= 0; --a, ++st) {
+                long long inner = 1;
+                for (int q = a + 1; q < p->d; ++q) inner *= p->n[q];
+                SweepJob j;
+                j.transform = i;
+                j.axis = a;
+                j.stage = st;
+                j.log2L = p->axes[a].log2L;
+                j.strided = inner > 1;
+                j.fused = (prec == JT_FP32) && jt::f32_warp_path(j.log2L);
+                j.nfib = total / p->n[a];
+                j.inner = inner;
+                sweeps.push_back(j);
+                max_stage = std::max(max_stage, st);
+            }
+        }
+        std::vector<jt::dev::BatchJob> hjobs;
+        for (int st = 0; st <= max_stage; ++st) {
+            // fused groups: (log2L, strided) -> jobs
+            for (int lg = jt::F32_WARP_MIN_LOG2L; lg <= jt::F32_WARP_MAX_LOG2L; ++lg)
+                for (int sk = 0; sk < 2; ++sk) {
+                    std::vector<const SweepJob*> grp;
+                    for (const auto& j : sweeps)
+                        if (j.fused && j.stage == st && j.log2L == lg && (int)j.strided == sk) grp.push_back(&j);
+                    for (size_t c0 = 0; c0 < grp.size(); c0 += jt::dev::BATCH_MAX_JOBS) {
+                        jt_batch::Launch L;
+                        L.fused = true;
+                        L.stage = st;
+                        L.log2L = lg;
+                        L.strided = sk != 0;
+                        L.job_off = (int)hjobs.size();
+                        const int ft = jt::f32_warp_tile_fibres(lg);
+                        for (size_t q = c0; q < std::min(grp.size(), c0 + jt::dev::BATCH_MAX_JOBS); ++q) {
+                            const SweepJob& j = *grp[q];
+                            jt::dev::BatchJob bj{};
+                            bj.A = plans[j.transform]->axes[j.axis].dev;
+                            bj.nfib = j.nfib;
+                            bj.inner = j.inner;
+                            bj.tile_begin = L.total_tiles;
+                            bj.slot = (int)L.slot_transform.size();
+                            L.slot_transform.push_back(j.transform);
+                            L.total_tiles += (j.nfib + ft - 1) / ft;
+                            hjobs.push_back(bj);
+                        }
+                        L.njobs = (int)hjobs.size() - L.job_off;
+                        b->launches.push_back(L);
+                    }
+                }
+            for (const auto& j : sweeps) {
+                if (j.fused || j.stage != st) continue;
+                jt_batch::Launch L;
+                L.stage = st;
+                L.transform = j.transform;
+                L.axis = j.axis;
+                L.nfib = j.nfib;
+                L.inner = j.inner;
+                b->launches.push_back(L);
+            }
+        }
+        if (!hjobs.empty()) {
+            if (cudaMalloc((void**)&b->d_jobs, sizeof(jt::dev::BatchJob) * hjobs.size()) != cudaSuccess) {
+                cudaGetLastError();
+                delete b;
+                return JT_ENOMEM;
+            }
+            cudaStream_t s = (cudaStream_t)stream;
+            if (cudaMemcpyAsync(b->d_jobs, hjobs.data(), sizeof(jt::dev::BatchJob) * hjobs.size(),
+                                cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                jt_batch_destroy(b);
+                return JT_ECUDA;
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        jt_batch_destroy(b);
+        return JT_ENOMEM;
+    } catch (...) {
+        jt_batch_destroy(b);
+        return JT_EINVAL;
+    }
+    *out = b;
+    return JT_OK;
+}
+
+jt_status jt_batch_forward(jt_batch* batch, const void* const* in, void* const* out, jt_stream_t stream) {
+    return batch_run(batch, in, out, true, (cudaStream_t)stream);
+}
+
+jt_status jt_batch_adjoint(jt_batch* batch, const void* const* in, void* const* out, jt_stream_t stream) {
+    return batch_run(batch, in, out, false, (cudaStream_t)stream);
+}
+
+void jt_batch_destroy(jt_batch* batch) {
+    if (!batch) return;
+    if (batch->d_jobs) cudaFree(batch->d_jobs);
+    delete batch;
+}
 
 jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a, const double* b,
                          const double* const* points, double eps, const jt_options* opt, jt_stream_t stream) {

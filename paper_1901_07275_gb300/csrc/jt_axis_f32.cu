@@ -28,7 +28,8 @@ static cudaError_t launch_warp(const dev::AxisDev& A, const float* in, float* ou
     long long ntiles = (nfib + S::FT - 1) / S::FT;
     long long grid = std::min<long long>(ntiles, (long long)num_sms * blocks_per_sm);
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, S::THREADS, smem, s>>>(A, in, out, nfib, inner);
+    static const dev::BatchPtrs no_ptrs{};
+    kern<<<(unsigned)grid, S::THREADS, smem, s>>>(A, in, out, nfib, inner, nullptr, 0, 0, no_ptrs);
     return cudaGetLastError();
 }
 
@@ -46,6 +47,8 @@ static cudaError_t warp_dispatch(int log2L, const dev::AxisDev& A, bool fwd, con
     if constexpr (LOG2L > F32_WARP_MIN_LOG2L) return warp_dispatch<LOG2L - 1>(log2L, A, fwd, in, out, nfib, inner, s);
     return cudaErrorInvalidValue;
 }
+
+int f32_warp_tile_fibres(int log2L) { return 256 >> (log2L - 4); }
 
 cudaError_t launch_axis_f32(const dev::AxisDev& A, int log2L, bool fwd, const float* in, float* out,
                             long long nfib, long long inner, cudaStream_t s) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "jt_axis.cuh"
+#include "jt_warp.cuh"
 
 namespace jt {
 
@@ -13,6 +14,13 @@ cudaError_t launch_axis_f32(const dev::AxisDev& A, int log2L, bool fwd, const fl
                             long long nfib, long long inner, cudaStream_t s);
 cudaError_t launch_axis_dw(const dev::AxisDev& A, int log2L, bool fwd, const double* in, double* out,
                            long long nfib, long long inner, cudaStream_t s);
+
+// One launch of the four-step kernel over the concatenated tiles of several jobs of the same
+// FFT length, direction and stride kind (jobs: a device array ordered by tile_begin).
+cudaError_t launch_axis_f32_batched(int log2L, bool fwd, bool strided, const dev::BatchJob* jobs, int njobs,
+                                    long long total_tiles, const dev::BatchPtrs& ptrs, cudaStream_t s);
+// Fibres per CTA tile of the four-step kernel (tile counting for batched jobs).
+int f32_warp_tile_fibres(int log2L);
 
 constexpr int MAX_LOG2L_F32 = 14;
 constexpr int MAX_LOG2L_DW = 13;

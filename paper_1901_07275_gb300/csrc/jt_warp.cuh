@@ -108,10 +108,28 @@ struct Own {
     }
 };
 
-// One forward or adjoint sweep over nfib fibres (see jt_axis.cuh for the operator).
-template <int LOG2L, bool FWD, bool STRIDED>
+// One sweep of one axis of one transform, as an entry of a batched launch: the CTA tiles of
+// all jobs of a launch are numbered consecutively, job i owning [tile_begin, tile_begin + tiles).
+// The job tables are built once per batch; the caller's array pointers of one launch travel as
+// a by-value kernel parameter (BatchPtrs), so a launch needs no host-to-device copy.
+constexpr int BATCH_MAX_JOBS = 256;
+struct BatchJob {
+    AxisDev A;
+    long long nfib, inner, tile_begin;
+    int slot;  // index into BatchPtrs
+};
+struct BatchPtrs {
+    const float* in[BATCH_MAX_JOBS];
+    float* out[BATCH_MAX_JOBS];
+};
+
+// One forward or adjoint sweep over nfib fibres (see jt_axis.cuh for the operator).  With
+// BATCHED, the kernel walks the concatenated tiles of njobs jobs instead (same arithmetic;
+// the per-job constants are reloaded when a CTA moves on to the next job).
+template <int LOG2L, bool FWD, bool STRIDED, bool BATCHED = false>
 __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
-    warp_axis_kernel(AxisDev A, const float* in, float* out, long long nfib, long long inner) {
+    warp_axis_kernel(AxisDev A, const float* in, float* out, long long nfib, long long inner,
+                     const BatchJob* __restrict__ jobs, int njobs, long long total_tiles, const __grid_constant__ BatchPtrs ptrs) {
     using S = WShape<LOG2L>;
     constexpr int L = S::L, T = S::T, FT = S::FT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -122,39 +140,79 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     float* aux = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)fl * S::AUX;
     float* tile = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)FT * S::AUX;
 
-    const int n = A.n, nu0 = A.nu0, rank = A.rank;
+    if constexpr (BATCHED) {
+        if (njobs <= 0) return;
+        A = jobs[0].A;  // replaced below by the job of the first tile
+    }
+    int n = A.n, nu0 = A.nu0, rank = A.rank;
     const float2* __restrict__ vtab = reinterpret_cast<const float2*>(A.vtab);
     const float2* __restrict__ utab = reinterpret_cast<const float2*>(A.utab);
     const float* __restrict__ vblk = reinterpret_cast<const float*>(A.vblk);  // [c][0..L), zero beyond n
     const float2* __restrict__ tw = reinterpret_cast<const float2*>(A.twid);
     const float2* __restrict__ ubtab = reinterpret_cast<const float2*>(A.ubtab);
 
-    // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane
+    // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane (they depend on L only)
     Cx<float> twA[16];
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) twA[k1] = cx(__ldg(tw + ((t * k1) & (L - 1))));
-    // Per-lane constants.  Forward: padded gather-buffer index of each owned point, two 16-bit
-    // fields a word.  Adjoint: whether one of the lane's bins holds more than two points.
+    // Per-lane constants of one job.  Forward: padded gather-buffer index of each owned point,
+    // two 16-bit fields a word.  Adjoint: whether one of the lane's bins holds more than two points.
     constexpr int NPK = FWD ? 8 : 1;
     unsigned pk[NPK];
+    bool sorted = false;
+    auto load_job_constants = [&]() {
+        n = A.n;
+        nu0 = A.nu0;
+        rank = A.rank;
+        vtab = reinterpret_cast<const float2*>(A.vtab);
+        utab = reinterpret_cast<const float2*>(A.utab);
+        vblk = reinterpret_cast<const float*>(A.vblk);
+        ubtab = reinterpret_cast<const float2*>(A.ubtab);
 #pragma unroll
-    for (int i = 0; i < NPK; ++i) {
-        if constexpr (FWD) {
-            unsigned v[2] = {0u, 0u};
+        for (int i = 0; i < NPK; ++i) {
+            if constexpr (FWD) {
+                unsigned v[2] = {0u, 0u};
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = t + T * (2 * i + h);
-                if (j < n) v[h] = (unsigned)S::ypad(__ldg(A.mtab + j));
+                for (int h = 0; h < 2; ++h) {
+                    const int j = t + T * (2 * i + h);
+                    if (j < n) v[h] = (unsigned)S::ypad(__ldg(A.mtab + j));
+                }
+                pk[i] = v[0] | (v[1] << 16);
+            } else {
+                pk[i] = (unsigned)__ldg(A.ovftab + t);
             }
-            pk[i] = v[0] | (v[1] << 16);
-        } else {
-            pk[i] = (unsigned)__ldg(A.ovftab + t);
         }
-    }
-    const bool sorted = A.sorted != 0;
+        sorted = A.sorted != 0;
+    };
+    int cur_job = -1;
+    if constexpr (!BATCHED) load_job_constants();
 
-    const long long ntiles = (nfib + FT - 1) / FT;
-    for (long long tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
+    const long long ntiles = BATCHED ? total_tiles : (nfib + FT - 1) / FT;
+    for (long long g_tile = blockIdx.x; g_tile < ntiles; g_tile += gridDim.x) {
+        long long tile_i = g_tile;
+        if constexpr (BATCHED) {
+            // jobs are ordered by tile_begin and a CTA's tiles increase: advance, or search once
+            int j = cur_job < 0 ? 0 : cur_job;
+            if (cur_job < 0) {
+                int lo = 0, hi = njobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (jobs[mid].tile_begin <= g_tile) lo = mid; else hi = mid - 1;
+                }
+                j = lo;
+            }
+            while (j + 1 < njobs && jobs[j + 1].tile_begin <= g_tile) ++j;
+            if (j != cur_job) {
+                A = jobs[j].A;
+                in = ptrs.in[jobs[j].slot];
+                out = ptrs.out[jobs[j].slot];
+                nfib = jobs[j].nfib;
+                inner = jobs[j].inner;
+                load_job_constants();
+                cur_job = j;
+            }
+            tile_i = g_tile - jobs[j].tile_begin;
+        }
         const long long f0 = tile_i * FT;
         const long long f = f0 + fl;
         const bool valid = f < nfib;

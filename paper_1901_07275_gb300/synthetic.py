@@ -110,3 +110,19 @@ def workload(name: str, nrhs: int = 1) -> dict:
         "alpha": alpha,
         "y": normal(seed, 1, shape) if name == "2d-nonuniform-1024" else None,
     }
+
+
+def batch_mix(count: int = 512, seed: int = 1004, n1=(256, 16384), n2=(64, 1024), max_rhs: int = 16):
+    """The serving-style mix: ``count`` members, a fair coin between 1-D and 2-D; 1-D n
+    log-uniform in ``n1``, 2-D n_x, n_y drawn independently log-uniform in ``n2``; (a, b)
+    uniform in (-0.5, 0.5) per axis; nrhs uniform in 1..max_rhs.  Returns a list of dicts
+    with ``n``, ``ab`` and ``nrhs`` (coefficients are drawn by the caller per member)."""
+    u = uniform(seed, 5, (count, 8))
+    members = []
+    for i in range(count):
+        two = u[i, 0] < 0.5
+        lo, hi = (n2 if two else n1)
+        ns = [int(round(np.exp(np.log(lo) + u[i, 1 + k] * (np.log(hi) - np.log(lo))))) for k in range(2 if two else 1)]
+        ab = [(float(u[i, 3 + 2 * k] - 0.5), float(u[i, 4 + 2 * k] - 0.5)) for k in range(len(ns))]
+        members.append({"n": ns, "ab": ab, "nrhs": 1 + int(u[i, 7] * max_rhs)})
+    return members

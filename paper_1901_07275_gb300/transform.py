@@ -112,6 +112,50 @@ class Transform:
             pass
 
 
+class Batch:
+    """Several transforms of one precision executed together (``jt_batch_*``): each member
+    has its own :class:`Transform` and number of right-hand sides; ``forward`` and
+    ``adjoint`` take lists of tensors, one per member, shaped ``(nrhs_i, *n_i)``."""
+
+    def __init__(self, transforms, nrhs, stream=None):
+        self.transforms = list(transforms)
+        self.nrhs = [int(v) for v in nrhs]
+        if len(self.transforms) != len(self.nrhs) or not self.transforms:
+            raise ValueError("one nrhs per transform")
+        self._batch = B.jt_batch_create([t._plan for t in self.transforms], self.nrhs,
+                                        Transform._stream(stream))
+
+    def _run(self, fn, xs, outs, stream):
+        import torch
+
+        if len(xs) != len(self.transforms):
+            raise ValueError("one input per member")
+        if outs is None:
+            outs = [torch.empty_like(x) for x in xs]
+        for T, r, x, o in zip(self.transforms, self.nrhs, xs, outs):
+            if T._check(x) != r or T._check(o) != r:
+                raise ValueError("input or output does not match the member's nrhs")
+        fn(self._batch, [x.data_ptr() for x in xs], [o.data_ptr() for o in outs], Transform._stream(stream))
+        return outs
+
+    def forward(self, xs, outs=None, stream=None):
+        return self._run(B.jt_batch_forward, xs, outs, stream)
+
+    def adjoint(self, gs, outs=None, stream=None):
+        return self._run(B.jt_batch_adjoint, gs, outs, stream)
+
+    def close(self):
+        if getattr(self, "_batch", None):
+            B.jt_batch_destroy(self._batch)
+            self._batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _make_fn():
     import torch
 
