@@ -286,6 +286,66 @@ def other_configs(dev, stream):
     return out
 
 
+def batch_mix_throughput(dev, stream, count=64):
+    """The serving-style mix (1-D n log-uniform in [256, 16384] or 2-D n_x, n_y in [64, 1024],
+    (a, b) ~ U(-0.5, 0.5), 1..16 right-hand sides), FP32: one batched forward + adjoint per
+    step, eager and replayed from a CUDA graph, against the members launched one by one."""
+    import torch
+
+    from paper_1901_07275_gb300 import Batch, Transform
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    t0 = time.perf_counter()
+    mix = syn.batch_mix(count)
+    Ts = [Transform(m["n"], [p[0] for p in m["ab"]], [p[1] for p in m["ab"]], eps=1e-7) for m in mix]
+    setup_s = time.perf_counter() - t0
+    xs = [torch.tensor(syn.normal(2000 + i, 0, (m["nrhs"],) + tuple(m["n"])), dtype=torch.float32, device=dev)
+          for i, m in enumerate(mix)]
+    fs = [torch.empty_like(x) for x in xs]
+    gs = [torch.empty_like(x) for x in xs]
+    batch = Batch(Ts, [m["nrhs"] for m in mix])
+    coeffs = 2 * sum(x.numel() for x in xs)
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def batched():
+        batch.forward(xs, fs)
+        batch.adjoint(fs, gs)
+
+    def one_by_one():
+        for T, x, f, g in zip(Ts, xs, fs, gs):
+            T.forward(x, out=f)
+            T.adjoint(f, out=g)
+
+    ms_batch = timed(batched)
+    ms_single = timed(one_by_one)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=side):
+        batch.forward(xs, fs, stream=side)
+        batch.adjoint(fs, gs, stream=side)
+    ms_graph = timed(graph.replay)
+    out = {"members": count, "coeffs_per_step": coeffs, "plan_setup_s": setup_s,
+           "batched": {"coeffs_per_s": coeffs / (ms_batch * 1e-3), "ms_per_step": ms_batch},
+           "graph_replay": {"coeffs_per_s": coeffs / (ms_graph * 1e-3), "ms_per_step": ms_graph},
+           "one_by_one": {"coeffs_per_s": coeffs / (ms_single * 1e-3), "ms_per_step": ms_single}}
+    batch.close()
+    for T in Ts:
+        T.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,6 +531,7 @@ def main():
         Tp.close()
 
         line["other_configs"] = other_configs(dev, stream)
+        line["batch"] = batch_mix_throughput(dev, stream)
 
         if world == 1:
             line["cpu_baseline"] = oracle_throughput(nrhs)
