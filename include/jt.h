@@ -69,7 +69,9 @@ typedef struct {
     int32_t oversample_q;   /* oversampling factor q of Algorithm 2.1; default 3 */
     uint64_t seed;          /* seed of the row/column sampling in Algorithm 2.1 */
     int32_t fft_len_policy; /* 0: L = n if n is a power of two, else the next power of two */
-    int32_t autotune;       /* reserved, must be 0 */
+    int32_t autotune;       /* 0: rank splits by the occupancy rule (see jt_plan_set_ksplit);
+                               1: jt_batch_create measures them for every member sweep
+                               (as jt_plan_tune does) before building the batch */
 } jt_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -140,18 +142,53 @@ jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_le
 void jt_destroy(jt_plan* plan);
 
 /* ------------------------------------------------------------------------------------
+ * Schedules (no counterpart in the paper, which applies the rank terms one after another
+ * on one processor): the rank split of an axis sweep is the number of CTAs (a thread-block
+ * cluster, 1, 2, 4 or 8) that share a tile of fibres, each applying a contiguous share of
+ * the r rank terms of Eq. eq:oneJ / eq:oneJinv; the partial sums are added in distributed
+ * shared memory in a fixed order, so a given split gives reproducible results (different
+ * splits agree to rounding).  Splitting shortens the critical path of sweeps with few
+ * fibres (large n, few right-hand sides) that cannot fill the GPU otherwise.
+ * Order of precedence for a sweep of F fibres: a split measured by jt_plan_tune for F
+ * fibres, then one fixed by jt_plan_set_ksplit, then the occupancy rule (double the split,
+ * up to 8, while the split tiles fit in one wave and every CTA keeps a rank term).
+ * These calls change the plan: do not make them while other calls use the plan.
+ * JT_FP64_PLAIN plans have no schedule: JT_ENOTSUP.
+ * ------------------------------------------------------------------------------------ */
+
+/* Fix the rank split of axis `axis` (-1: every axis) for `direction` 0 = forward,
+ * 1 = adjoint/inverse, -1 = both.  ksplit in {0 (occupancy rule), 1, 2, 4, 8}, else
+ * JT_EINVAL.  Drops measured splits of the same axes and directions. */
+jt_status jt_plan_set_ksplit(jt_plan* plan, int axis, int direction, int ksplit);
+
+/* Measure, for nrhs right-hand sides, every split in {1, 2, 4, 8} (at most the rank) of
+ * every axis sweep in both directions and keep the fastest.  Allocates and frees two
+ * scratch arrays of nrhs * prod(n) elements, launches the sweeps on `stream` and
+ * synchronises it.  JT_EINVAL if the stream is being captured into a graph. */
+jt_status jt_plan_tune(jt_plan* plan, int64_t nrhs, jt_stream_t stream);
+
+/* The rank split the sweep of axis `axis` gets in `direction` (0 forward, 1 adjoint) for
+ * nrhs right-hand sides (the launchers may fall back to a smaller cluster if one of that
+ * size cannot be resident). */
+jt_status jt_plan_schedule(const jt_plan* plan, int axis, int direction, int64_t nrhs, int* ksplit);
+
+/* ------------------------------------------------------------------------------------
  * Batches: many transforms of one precision (JT_FP32 or JT_SPLIT), each with its own plan
  * (any d, n, a, b, points) and number of right-hand sides, executed together.  The axis
  * sweeps are grouped by stage (the s-th sweep of every transform, Sec. 3.2-3.3) and, within
- * a stage, by FFT length and stride kind; FP32 sweeps of length 16..4096 of one group run as
- * a single kernel launch over all their fibres, other sweeps one launch each.
+ * a stage, by FFT length, stride kind and rank split; FP32 sweeps of length 16..4096 of one
+ * group run as a single kernel launch over all their fibres, other sweeps one launch each.
  * ------------------------------------------------------------------------------------ */
 typedef struct jt_batch jt_batch;
 
 /* Build the schedule of a batch of `count` plans (not owned; they must outlive the batch)
  * with nrhs[i] >= 1 right-hand sides each; uploads the job tables on `stream` and
- * synchronises it.  JT_EINVAL for mixed precisions or bad arguments, JT_ENOTSUP for
- * JT_FP64_PLAIN plans. */
+ * synchronises it.  Each member sweep keeps its plan's rank split for that many fibres
+ * (see jt_plan_schedule; measured first for plans created with autotune = 1); sweeps with
+ * different splits go to different launches.  The launches of one stage are spread over
+ * four worker streams that the batch owns, forked from and joined back to the caller's
+ * stream on every execution.  JT_EINVAL for mixed precisions or bad arguments, JT_ENOTSUP
+ * for JT_FP64_PLAIN plans. */
 jt_status jt_batch_create(jt_batch** out, int count, jt_plan* const* plans, const int64_t* nrhs,
                           jt_stream_t stream);
 

@@ -29,6 +29,9 @@ EXPORTS = (
     "jt_forward_plain_noalloc",
     "jt_plan_info",
     "jt_destroy",
+    "jt_plan_set_ksplit",
+    "jt_plan_tune",
+    "jt_plan_schedule",
     "jt_batch_create",
     "jt_batch_forward",
     "jt_batch_adjoint",
@@ -86,6 +89,12 @@ def lib() -> ctypes.CDLL:
     L.jt_plan_info.restype = i32
     L.jt_destroy.argtypes = [vp]
     L.jt_destroy.restype = None
+    L.jt_plan_set_ksplit.argtypes = [vp, i32, i32, i32]
+    L.jt_plan_set_ksplit.restype = i32
+    L.jt_plan_tune.argtypes = [vp, i64, vp]
+    L.jt_plan_tune.restype = i32
+    L.jt_plan_schedule.argtypes = [vp, i32, i32, i64, ctypes.POINTER(i32)]
+    L.jt_plan_schedule.restype = i32
     L.jt_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64), vp]
     L.jt_batch_create.restype = i32
     for name in ("jt_batch_forward", "jt_batch_adjoint"):
@@ -120,13 +129,14 @@ def _check(status: int, what: str):
         raise JTError(status, what)
 
 
-def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None) -> Options:
+def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None, autotune=0) -> Options:
     o = Options()
     lib().jt_options_default(ctypes.byref(o))
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     o.nu0 = nu0
     o.rank_cap = rank_cap
     o.oversample_q = oversample_q
+    o.autotune = int(autotune)
     if seed is not None:
         o.seed = seed
     return o
@@ -195,6 +205,25 @@ def jt_plan_info(plan: int, axis: int, n: int | None = None):
 
 def jt_destroy(plan: int) -> None:
     lib().jt_destroy(_ptr(plan))
+
+
+def jt_plan_set_ksplit(plan: int, axis: int, direction: int, ksplit: int) -> None:
+    """Fix the rank split (CTAs per tile) of axis ``axis`` (-1: all) for ``direction``
+    (0 forward, 1 adjoint, -1 both); 0 restores the occupancy rule."""
+    _check(lib().jt_plan_set_ksplit(_ptr(plan), int(axis), int(direction), int(ksplit)), "jt_plan_set_ksplit")
+
+
+def jt_plan_tune(plan: int, nrhs: int, stream: int = 0) -> None:
+    """Measure and keep the fastest rank split of every sweep for ``nrhs`` right-hand sides."""
+    _check(lib().jt_plan_tune(_ptr(plan), int(nrhs), _ptr(stream)), "jt_plan_tune")
+
+
+def jt_plan_schedule(plan: int, axis: int, direction: int, nrhs: int) -> int:
+    """The rank split the sweep of ``axis`` gets in ``direction`` for ``nrhs`` right-hand sides."""
+    k = ctypes.c_int()
+    _check(lib().jt_plan_schedule(_ptr(plan), int(axis), int(direction), int(nrhs), ctypes.byref(k)),
+           "jt_plan_schedule")
+    return k.value
 
 
 def jt_batch_create(plans, nrhs, stream: int = 0) -> int:

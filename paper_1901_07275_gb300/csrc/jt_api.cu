@@ -42,6 +42,17 @@ struct jt_plan {
     int64_t n[3] = {1, 1, 1};
     std::vector<DeviceAxis> axes;
     jt::PlainPlan* plain = nullptr;  // JT_FP64_PLAIN resources
+    // Schedules of the fused sweeps: the rank split (CTAs per tile) of each (axis, direction).
+    // A measured choice for a sweep of that many fibres (jt_plan_tune) comes first, then a
+    // fixed one (jt_plan_set_ksplit), then the occupancy rule of the launchers.
+    int ksplit_fixed[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    bool autotune = false;  // jt_batch_create measures the splits of this plan's sweeps
+    struct Tuned {
+        int axis, fwd;
+        long long nfib;
+        int ksplit;
+    };
+    std::vector<Tuned> tuned;
 };
 
 namespace {
@@ -175,6 +186,25 @@ void free_axis(DeviceAxis& ax) {
     ax.allocs.clear();
 }
 
+// Rank split of the sweep of axis ax over nfib fibres.
+int sweep_ksplit(const jt_plan* plan, int ax, bool fwd, long long nfib, bool strided) {
+    for (const auto& t : plan->tuned)
+        if (t.axis == ax && t.fwd == (int)fwd && t.nfib == nfib) return t.ksplit;
+    const int fixed = plan->ksplit_fixed[ax][fwd ? 0 : 1];
+    if (fixed > 0) return fixed;
+    const DeviceAxis& A = plan->axes[ax];
+    if (plan->prec == JT_FP32) return jt::auto_ksplit_f32(A.log2L, fwd, strided, nfib, A.dev.rank);
+    return jt::auto_ksplit_dw(A.log2L, fwd, nfib, A.dev.rank);
+}
+
+cudaError_t launch_sweep(const jt_plan* plan, int ax, bool fwd, const void* src, void* dst, long long nfib,
+                         long long inner, int ksplit, cudaStream_t s) {
+    const DeviceAxis& A = plan->axes[ax];
+    if (plan->prec == JT_FP32)
+        return jt::launch_axis_f32(A.dev, A.log2L, fwd, (const float*)src, (float*)dst, nfib, inner, ksplit, s);
+    return jt::launch_axis_dw(A.dev, A.log2L, fwd, (const double*)src, (double*)dst, nfib, inner, ksplit, s);
+}
+
 // Sweep every axis (last axis first).  Sweep 0 maps in -> out; later sweeps run in place.
 template <class IO>
 jt_status sweep(jt_plan* plan, const IO* in, IO* out, int64_t nrhs, bool fwd, cudaStream_t s) {
@@ -186,13 +216,8 @@ jt_status sweep(jt_plan* plan, const IO* in, IO* out, int64_t nrhs, bool fwd, cu
         int64_t inner = 1;
         for (int i = ax + 1; i < d; ++i) inner *= plan->n[i];
         const int64_t nfib = total / plan->n[ax];
-        const DeviceAxis& A = plan->axes[ax];
-        cudaError_t e;
-        if constexpr (sizeof(IO) == 4)
-            e = jt::launch_axis_f32(A.dev, A.log2L, fwd, (const float*)src, (float*)out, nfib, inner, s);
-        else
-            e = jt::launch_axis_dw(A.dev, A.log2L, fwd, (const double*)src, (double*)out, nfib, inner, s);
-        if (e != cudaSuccess) return JT_ECUDA;
+        const int ks = sweep_ksplit(plan, ax, fwd, nfib, inner > 1);
+        if (launch_sweep(plan, ax, fwd, src, out, nfib, inner, ks, s) != cudaSuccess) return JT_ECUDA;
         src = out;
     }
     return JT_OK;
@@ -218,19 +243,95 @@ jt_status apply(jt_plan* plan, const void* in, void* out, int64_t nrhs, bool fwd
 
 }  // namespace
 
+// Total elements of nrhs right-hand sides, or -1 past the addressing limit.
+int64_t plan_elements(const jt_plan* plan, int64_t nrhs) {
+    int64_t total = nrhs;
+    for (int i = 0; i < plan->d; ++i) {
+        if (total > (int64_t(1) << 40) / plan->n[i]) return -1;
+        total *= plan->n[i];
+    }
+    return total;
+}
+
+// Measure the rank splits of every sweep of `plan` for nrhs right-hand sides (see
+// jt_plan_tune) and record the fastest of each.
+jt_status tune_plan(jt_plan* plan, int64_t nrhs, cudaStream_t s) {
+    const int64_t total = plan_elements(plan, nrhs);
+    if (total < 1) return JT_EINVAL;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return JT_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return JT_EINVAL;
+    const size_t bytes = (size_t)total * (plan->prec == JT_FP32 ? 4 : 8);
+    void *x = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    jt_status st = JT_OK;
+    if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        st = JT_ENOMEM;
+    } else if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+               cudaMemsetAsync(x, 0, bytes, s) != cudaSuccess) {
+        st = JT_ECUDA;
+    }
+    for (int ax = plan->d - 1; st == JT_OK && ax >= 0; --ax) {
+        long long inner = 1;
+        for (int i = ax + 1; i < plan->d; ++i) inner *= plan->n[i];
+        const long long nfib = total / plan->n[ax];
+        const int rank = plan->axes[ax].dev.rank;
+        for (int dir = 0; st == JT_OK && dir < 2; ++dir) {
+            const bool fwd = dir == 0;
+            int best = 1;
+            float best_ms = 0.0f;
+            for (int ks = 1; ks <= 8 && (ks == 1 || ks <= rank); ks *= 2) {
+                float ms = 0.0f;
+                if (launch_sweep(plan, ax, fwd, x, y, nfib, inner, ks, s) != cudaSuccess ||
+                    cudaEventRecord(e0, s) != cudaSuccess) {
+                    st = JT_ECUDA;
+                    break;
+                }
+                for (int rep = 0; rep < 3 && st == JT_OK; ++rep)
+                    if (launch_sweep(plan, ax, fwd, x, y, nfib, inner, ks, s) != cudaSuccess) st = JT_ECUDA;
+                if (st != JT_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    st = JT_ECUDA;
+                    break;
+                }
+                if (ks == 1 || ms < best_ms) {
+                    best = ks;
+                    best_ms = ms;
+                }
+            }
+            if (st != JT_OK) break;
+            auto& tv = plan->tuned;
+            tv.erase(std::remove_if(tv.begin(), tv.end(),
+                                    [&](const jt_plan::Tuned& t) { return t.axis == ax && t.fwd == (int)fwd && t.nfib == nfib; }),
+                     tv.end());
+            tv.push_back({ax, (int)fwd, nfib, best});
+        }
+    }
+    if (st == JT_OK && cudaStreamSynchronize(s) != cudaSuccess) st = JT_ECUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (x) cudaFree(x);
+    if (y) cudaFree(y);
+    return st;
+}
+
 // A batch: the axis sweeps of several plans, grouped by stage (the s-th sweep of every
-// transform) and, inside a stage, by FFT length and stride kind.  FP32 sweeps of length
-// 16..4096 run as one launch per group (at most BATCH_MAX_JOBS jobs a launch); every other
-// sweep is launched on its own.  Nothing is allocated or copied at execution, so an execution
-// can be captured in a CUDA graph.
+// transform) and, inside a stage, by FFT length, stride kind and rank split.  FP32 sweeps of
+// length 16..4096 run as one launch per group (at most BATCH_MAX_JOBS jobs a launch); every
+// other sweep is launched on its own.  The launches of a stage are spread over a few worker
+// streams (forked from and joined back to the caller's stream, with a barrier between
+// stages), so that small launches run side by side.  Nothing is allocated or copied at
+// execution, so an execution can be captured in a CUDA graph.
 struct jt_batch {
+    static constexpr int WORKERS = 4;
     int count = 0;
     int prec = JT_FP32;
     std::vector<jt_plan*> plans;
     std::vector<int64_t> nrhs;
     struct Launch {
         bool fused = false;
-        int stage = 0, log2L = 0;
+        int stage = 0, log2L = 0, ksplit = 1, worker = 0;
         bool strided = false;
         // fused: device jobs [job_off, job_off + njobs), slot -> transform index
         int job_off = 0, njobs = 0;
@@ -239,24 +340,43 @@ struct jt_batch {
         // single: transform index and axis
         int transform = 0, axis = 0;
         long long nfib = 0, inner = 1;
+        double cost = 0;  // relative work, for spreading a stage over the workers
     };
-    std::vector<Launch> launches;
+    std::vector<Launch> launches[2];  // [0] forward, [1] adjoint; ordered by stage
     jt::dev::BatchJob* d_jobs = nullptr;
+    cudaStream_t work[WORKERS] = {};
+    cudaEvent_t ev_fork = nullptr, ev_stage[WORKERS] = {}, ev_join[WORKERS] = {};
 };
 
 namespace {
 
 struct SweepJob {
-    int transform, axis, stage, log2L;
+    int transform, axis, stage, log2L, ksplit;
     bool strided, fused;
     long long nfib, inner;
+    double cost;
 };
 
 jt_status batch_run(jt_batch* b, const void* const* in, void* const* out, bool fwd, cudaStream_t s) {
     if (!b || !in || !out) return JT_EINVAL;
     for (int i = 0; i < b->count; ++i)
         if (!in[i] || !out[i]) return JT_EINVAL;
-    for (const auto& L : b->launches) {
+    constexpr int W = jt_batch::WORKERS;
+    if (cudaEventRecord(b->ev_fork, s) != cudaSuccess) return JT_ECUDA;
+    for (int w = 0; w < W; ++w)
+        if (cudaStreamWaitEvent(b->work[w], b->ev_fork, 0) != cudaSuccess) return JT_ECUDA;
+    int stage = 0;
+    for (const auto& L : b->launches[fwd ? 0 : 1]) {
+        if (L.stage != stage) {
+            // stage barrier: every worker waits for the previous stage on all workers
+            for (int w = 0; w < W; ++w)
+                if (cudaEventRecord(b->ev_stage[w], b->work[w]) != cudaSuccess) return JT_ECUDA;
+            for (int w = 0; w < W; ++w)
+                for (int v = 0; v < W; ++v)
+                    if (v != w && cudaStreamWaitEvent(b->work[w], b->ev_stage[v], 0) != cudaSuccess) return JT_ECUDA;
+            stage = L.stage;
+        }
+        cudaStream_t ws = b->work[L.worker];
         cudaError_t e = cudaSuccess;
         if (L.fused) {
             jt::dev::BatchPtrs ptrs;
@@ -266,21 +386,84 @@ jt_status batch_run(jt_batch* b, const void* const* in, void* const* out, bool f
                 ptrs.out[q] = (float*)out[i];
             }
             e = jt::launch_axis_f32_batched(L.log2L, fwd, L.strided, b->d_jobs + L.job_off, L.njobs, L.total_tiles,
-                                            ptrs, s);
+                                            ptrs, L.ksplit, ws);
         } else {
-            const jt_plan* p = b->plans[L.transform];
-            const DeviceAxis& A = p->axes[L.axis];
             const void* src = (L.stage == 0) ? in[L.transform] : out[L.transform];
-            if (b->prec == JT_FP32)
-                e = jt::launch_axis_f32(A.dev, A.log2L, fwd, (const float*)src, (float*)out[L.transform], L.nfib,
-                                        L.inner, s);
-            else
-                e = jt::launch_axis_dw(A.dev, A.log2L, fwd, (const double*)src, (double*)out[L.transform], L.nfib,
-                                       L.inner, s);
+            e = launch_sweep(b->plans[L.transform], L.axis, fwd, src, out[L.transform], L.nfib, L.inner, L.ksplit, ws);
         }
         if (e != cudaSuccess) return JT_ECUDA;
     }
+    for (int w = 0; w < W; ++w) {
+        if (cudaEventRecord(b->ev_join[w], b->work[w]) != cudaSuccess) return JT_ECUDA;
+        if (cudaStreamWaitEvent(s, b->ev_join[w], 0) != cudaSuccess) return JT_ECUDA;
+    }
     return JT_OK;
+}
+
+// Launch lists of one direction: groups per stage, then the stage's launches spread over the
+// workers, largest first, each to the least loaded worker.
+void batch_plan_launches(jt_batch* b, bool fwd, const std::vector<SweepJob>& sweeps, int max_stage,
+                         std::vector<jt::dev::BatchJob>& hjobs) {
+    auto& out = b->launches[fwd ? 0 : 1];
+    for (int st = 0; st <= max_stage; ++st) {
+        std::vector<jt_batch::Launch> ls;
+        // fused groups: (log2L, strided, ksplit) -> jobs
+        for (int lg = jt::F32_WARP_MIN_LOG2L; lg <= jt::F32_WARP_MAX_LOG2L; ++lg)
+            for (int sk = 0; sk < 2; ++sk)
+                for (int ks = 1; ks <= 8; ks *= 2) {
+                    std::vector<const SweepJob*> grp;
+                    for (const auto& j : sweeps)
+                        if (j.fused && j.stage == st && j.log2L == lg && (int)j.strided == sk && j.ksplit == ks)
+                            grp.push_back(&j);
+                    for (size_t c0 = 0; c0 < grp.size(); c0 += jt::dev::BATCH_MAX_JOBS) {
+                        jt_batch::Launch L;
+                        L.fused = true;
+                        L.stage = st;
+                        L.log2L = lg;
+                        L.strided = sk != 0;
+                        L.ksplit = ks;
+                        L.job_off = (int)hjobs.size();
+                        const int ft = jt::f32_warp_tile_fibres(lg);
+                        for (size_t q = c0; q < std::min(grp.size(), c0 + jt::dev::BATCH_MAX_JOBS); ++q) {
+                            const SweepJob& j = *grp[q];
+                            jt::dev::BatchJob bj{};
+                            bj.A = b->plans[j.transform]->axes[j.axis].dev;
+                            bj.nfib = j.nfib;
+                            bj.inner = j.inner;
+                            bj.tile_begin = L.total_tiles;
+                            bj.slot = (int)L.slot_transform.size();
+                            L.slot_transform.push_back(j.transform);
+                            L.total_tiles += (j.nfib + ft - 1) / ft;
+                            L.cost += j.cost;
+                            hjobs.push_back(bj);
+                        }
+                        L.njobs = (int)hjobs.size() - L.job_off;
+                        ls.push_back(L);
+                    }
+                }
+        for (const auto& j : sweeps) {
+            if (j.fused || j.stage != st) continue;
+            jt_batch::Launch L;
+            L.stage = st;
+            L.transform = j.transform;
+            L.axis = j.axis;
+            L.nfib = j.nfib;
+            L.inner = j.inner;
+            L.ksplit = j.ksplit;
+            L.cost = j.cost;
+            ls.push_back(L);
+        }
+        std::stable_sort(ls.begin(), ls.end(), [](const jt_batch::Launch& x, const jt_batch::Launch& y) { return x.cost > y.cost; });
+        double load[jt_batch::WORKERS] = {};
+        for (auto& L : ls) {
+            int w = 0;
+            for (int v = 1; v < jt_batch::WORKERS; ++v)
+                if (load[v] < load[w]) w = v;
+            L.worker = w;
+            load[w] += L.cost;
+            out.push_back(std::move(L));
+        }
+    }
 }
 
 }  // namespace
@@ -304,76 +487,82 @@ jt_status jt_batch_create(jt_batch** out, int count, jt_plan* const* plans, cons
         b->prec = prec;
         b->plans.assign(plans, plans + count);
         b->nrhs.assign(nrhs, nrhs + count);
-        // sweeps of every transform, last axis first (the order of jt_forward)
-        std::vector<SweepJob> sweeps;
-        int max_stage = 0;
+        for (int w = 0; w < jt_batch::WORKERS; ++w) {
+            if (cudaStreamCreateWithFlags(&b->work[w], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ev_stage[w], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ev_join[w], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                jt_batch_destroy(b);
+                return JT_ECUDA;
+            }
+        }
+        if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            jt_batch_destroy(b);
+            return JT_ECUDA;
+        }
         for (int i = 0; i < count; ++i) {
-            const jt_plan* p = plans[i];
-            int64_t total = nrhs[i];
-            for (int a = 0; a < p->d; ++a) total *= p->n[a];
-            for (int a = p->d - 1, st = 0; a >= 0; --a, ++st) {
-                long long inner = 1;
-                for (int q = a + 1; q < p->d; ++q) inner *= p->n[q];
-                SweepJob j;
-                j.transform = i;
-                j.axis = a;
-                j.stage = st;
-                j.log2L = p->axes[a].log2L;
-                j.strided = inner > 1;
-                j.fused = (prec == JT_FP32) && jt::f32_warp_path(j.log2L);
-                j.nfib = total / p->n[a];
-                j.inner = inner;
-                sweeps.push_back(j);
-                max_stage = std::max(max_stage, st);
+            if (!plans[i]->autotune) continue;
+            const jt_status st = tune_plan(plans[i], nrhs[i], (cudaStream_t)stream);
+            if (st != JT_OK) {
+                jt_batch_destroy(b);
+                return st;
             }
         }
-        std::vector<jt::dev::BatchJob> hjobs;
-        for (int st = 0; st <= max_stage; ++st) {
-            // fused groups: (log2L, strided) -> jobs
-            for (int lg = jt::F32_WARP_MIN_LOG2L; lg <= jt::F32_WARP_MAX_LOG2L; ++lg)
-                for (int sk = 0; sk < 2; ++sk) {
-                    std::vector<const SweepJob*> grp;
-                    for (const auto& j : sweeps)
-                        if (j.fused && j.stage == st && j.log2L == lg && (int)j.strided == sk) grp.push_back(&j);
-                    for (size_t c0 = 0; c0 < grp.size(); c0 += jt::dev::BATCH_MAX_JOBS) {
-                        jt_batch::Launch L;
-                        L.fused = true;
-                        L.stage = st;
-                        L.log2L = lg;
-                        L.strided = sk != 0;
-                        L.job_off = (int)hjobs.size();
-                        const int ft = jt::f32_warp_tile_fibres(lg);
-                        for (size_t q = c0; q < std::min(grp.size(), c0 + jt::dev::BATCH_MAX_JOBS); ++q) {
-                            const SweepJob& j = *grp[q];
-                            jt::dev::BatchJob bj{};
-                            bj.A = plans[j.transform]->axes[j.axis].dev;
-                            bj.nfib = j.nfib;
-                            bj.inner = j.inner;
-                            bj.tile_begin = L.total_tiles;
-                            bj.slot = (int)L.slot_transform.size();
-                            L.slot_transform.push_back(j.transform);
-                            L.total_tiles += (j.nfib + ft - 1) / ft;
-                            hjobs.push_back(bj);
-                        }
-                        L.njobs = (int)hjobs.size() - L.job_off;
-                        b->launches.push_back(L);
-                    }
+        std::vector<jt::dev::BatchJob> hjobs;  // both directions, offsets global
+        for (int dir = 0; dir < 2; ++dir) {
+            const bool fwd = dir == 0;
+            // sweeps of every transform, last axis first (the order of jt_forward)
+            std::vector<SweepJob> sweeps;
+            int max_stage = 0;
+            for (int i = 0; i < count; ++i) {
+                const jt_plan* p = plans[i];
+                int64_t total = nrhs[i];
+                for (int a = 0; a < p->d; ++a) total *= p->n[a];
+                for (int a = p->d - 1, st = 0; a >= 0; --a, ++st) {
+                    long long inner = 1;
+                    for (int q = a + 1; q < p->d; ++q) inner *= p->n[q];
+                    SweepJob j;
+                    j.transform = i;
+                    j.axis = a;
+                    j.stage = st;
+                    j.log2L = p->axes[a].log2L;
+                    j.strided = inner > 1;
+                    j.fused = (prec == JT_FP32) && jt::f32_warp_path(j.log2L);
+                    j.nfib = total / p->n[a];
+                    j.inner = inner;
+                    j.ksplit = sweep_ksplit(p, a, fwd, j.nfib, j.strided);
+                    j.cost = (double)j.nfib * (double)std::max(1, p->axes[a].dev.rank) * (double)(int64_t(1) << j.log2L) *
+                             (double)std::max(1, j.log2L);
+                    sweeps.push_back(j);
+                    max_stage = std::max(max_stage, st);
                 }
-            for (const auto& j : sweeps) {
-                if (j.fused || j.stage != st) continue;
-                jt_batch::Launch L;
-                L.stage = st;
-                L.transform = j.transform;
-                L.axis = j.axis;
-                L.nfib = j.nfib;
-                L.inner = j.inner;
-                b->launches.push_back(L);
             }
+            batch_plan_launches(b, fwd, sweeps, max_stage, hjobs);
         }
+        // first use of each kernel instance (attributes, occupancy) here rather than at the
+        // first execution, which may be under stream capture: launches of zero tiles
+        for (int dir = 0; dir < 2; ++dir)
+            for (const auto& L : b->launches[dir]) {
+                cudaError_t e;
+                if (L.fused) {
+                    const jt::dev::BatchPtrs none{};
+                    e = jt::launch_axis_f32_batched(L.log2L, dir == 0, L.strided, nullptr, 0, 0, none, L.ksplit,
+                                                    (cudaStream_t)stream);
+                } else {
+                    e = launch_sweep(b->plans[L.transform], L.axis, dir == 0, nullptr, nullptr, 0, L.inner, L.ksplit,
+                                     (cudaStream_t)stream);
+                }
+                if (e != cudaSuccess) {
+                    jt_batch_destroy(b);
+                    return JT_ECUDA;
+                }
+            }
         if (!hjobs.empty()) {
+            static_assert(std::is_trivially_copyable<jt::dev::BatchJob>::value, "jobs are copied as bytes");
             if (cudaMalloc((void**)&b->d_jobs, sizeof(jt::dev::BatchJob) * hjobs.size()) != cudaSuccess) {
                 cudaGetLastError();
-                delete b;
+                jt_batch_destroy(b);
                 return JT_ENOMEM;
             }
             cudaStream_t s = (cudaStream_t)stream;
@@ -406,6 +595,12 @@ jt_status jt_batch_adjoint(jt_batch* batch, const void* const* in, void* const* 
 void jt_batch_destroy(jt_batch* batch) {
     if (!batch) return;
     if (batch->d_jobs) cudaFree(batch->d_jobs);
+    for (int w = 0; w < jt_batch::WORKERS; ++w) {
+        if (batch->work[w]) cudaStreamDestroy(batch->work[w]);
+        if (batch->ev_stage[w]) cudaEventDestroy(batch->ev_stage[w]);
+        if (batch->ev_join[w]) cudaEventDestroy(batch->ev_join[w]);
+    }
+    if (batch->ev_fork) cudaEventDestroy(batch->ev_fork);
     delete batch;
 }
 
@@ -430,6 +625,7 @@ jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a
         plan = new jt_plan();
         plan->d = d;
         plan->prec = o.prec;
+        plan->autotune = o.autotune != 0;
         plan->axes.resize(d);
         for (int i = 0; i < d; ++i) {
             plan->n[i] = n[i];
@@ -499,6 +695,45 @@ jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_le
     if (fft_len) *fft_len = T.L;
     if (t_out) std::memcpy(t_out, T.t.data(), sizeof(double) * T.n);
     if (w_out) std::memcpy(w_out, T.w.data(), sizeof(double) * T.n);
+    return JT_OK;
+}
+
+jt_status jt_plan_set_ksplit(jt_plan* plan, int axis, int direction, int ksplit) {
+    if (!plan || axis < -1 || axis >= plan->d || direction < -1 || direction > 1) return JT_EINVAL;
+    if (ksplit != 0 && ksplit != 1 && ksplit != 2 && ksplit != 4 && ksplit != 8) return JT_EINVAL;
+    if (plan->prec == JT_FP64_PLAIN) return JT_ENOTSUP;
+    for (int ax = 0; ax < plan->d; ++ax) {
+        if (axis >= 0 && ax != axis) continue;
+        for (int dir = 0; dir < 2; ++dir) {
+            if (direction >= 0 && dir != direction) continue;
+            plan->ksplit_fixed[ax][dir] = ksplit;
+            auto& tv = plan->tuned;
+            tv.erase(std::remove_if(tv.begin(), tv.end(),
+                                    [&](const jt_plan::Tuned& t) { return t.axis == ax && t.fwd == (dir == 0 ? 1 : 0); }),
+                     tv.end());
+        }
+    }
+    return JT_OK;
+}
+
+jt_status jt_plan_tune(jt_plan* plan, int64_t nrhs, jt_stream_t stream) {
+    if (!plan || nrhs < 1) return JT_EINVAL;
+    if (plan->prec == JT_FP64_PLAIN) return JT_ENOTSUP;
+    try {
+        return tune_plan(plan, nrhs, (cudaStream_t)stream);
+    } catch (...) {
+        return JT_ENOMEM;
+    }
+}
+
+jt_status jt_plan_schedule(const jt_plan* plan, int axis, int direction, int64_t nrhs, int* ksplit) {
+    if (!plan || !ksplit || axis < 0 || axis >= plan->d || direction < 0 || direction > 1 || nrhs < 1) return JT_EINVAL;
+    if (plan->prec == JT_FP64_PLAIN) return JT_ENOTSUP;
+    const int64_t total = plan_elements(plan, nrhs);
+    if (total < 1) return JT_EINVAL;
+    long long inner = 1;
+    for (int i = axis + 1; i < plan->d; ++i) inner *= plan->n[i];
+    *ksplit = sweep_ksplit(plan, axis, direction == 0, total / plan->n[axis], inner > 1);
     return JT_OK;
 }
 

@@ -288,6 +288,57 @@ struct AxisDev {
     const int* ovftab;   // [t]: 1 if a bin of lane t holds more than two points
 };
 
+// ------------------------------------------------------------------ clusters
+// Rank split: the CTAs of one thread-block cluster share a tile of fibres, CTA c of S taking
+// the rank terms [rank c / S, rank (c + 1) / S), and add their partial sums through
+// distributed shared memory.  A launch without a cluster attribute is a cluster of one CTA,
+// so the same code serves S = 1.
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_count() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster arrives; shared-memory writes made before it are
+// visible to the cluster's loads after it.  A hardware barrier: no software spin.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Load a float of CTA `rank`'s shared memory at the offset of `local` in this CTA's.
+__device__ __forceinline__ float ld_cluster(const float* local, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    float v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+    return v;
+}
+template <class R>
+__device__ __forceinline__ R ld_cluster_r(const R* local, unsigned rank);
+template <>
+__device__ __forceinline__ float ld_cluster_r<float>(const float* local, unsigned rank) {
+    return ld_cluster(local, rank);
+}
+template <>
+__device__ __forceinline__ dw ld_cluster_r<dw>(const dw* local, unsigned rank) {
+    const float* p = reinterpret_cast<const float*>(local);
+    return {ld_cluster(p, rank), ld_cluster(p + 1, rank)};
+}
+
 template <int T, int G>
 __device__ __forceinline__ void group_sync(int g) {
     if constexpr (T <= 32) {
@@ -363,13 +414,23 @@ __device__ __forceinline__ void fft(Cx<R>* x, R* sre, R* sim, const Cx<R>* __res
 }
 
 // ------------------------------------------------------------------ kernels
-template <class R, int LOG2L, bool FWD>
+// CTAs of 1024 threads get at most 64 registers a thread: those instances keep the fibre's
+// input in shared memory and read the bins from the (L1-resident) table instead of holding
+// both in registers.
+template <class R, int LOG2L>
+struct Lean {
+    static constexpr bool value = Shape<R, LOG2L>::THREADS >= 1024;
+};
+
+template <class R, int LOG2L, bool FWD, bool SPLIT = false>
 __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
     axis_kernel(AxisDev A, const typename RealOps<R>::io* in, typename RealOps<R>::io* out, long long nfib,
                 long long inner) {
     using S = Shape<R, LOG2L>;
     using IO = typename RealOps<R>::io;
     constexpr int L = S::L, E = S::E, T = S::T, G = S::G;
+    constexpr bool LEAN = Lean<R, LOG2L>::value;
+    constexpr int EV = LEAN ? 1 : E;  // register copies of the input
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* smem = reinterpret_cast<R*>(smem_raw);
     const int g = threadIdx.x / T;
@@ -385,9 +446,11 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
     const R* __restrict__ vblk = reinterpret_cast<const R*>(A.vblk);
     const Cx<R>* __restrict__ tw = reinterpret_cast<const Cx<R>*>(A.twid);
     const long long ntiles = (nfib + G - 1) / G;
+    const unsigned csize = SPLIT ? cluster_size() : 1u, crank = SPLIT ? cluster_rank() : 0u;
+    const int kb = (int)(((long long)rank * crank) / csize), ke = (int)(((long long)rank * (crank + 1)) / csize);
 
-    int mj[E];  // forward: bins of the owned output points
-    if constexpr (FWD) {
+    int mj[LEAN ? 1 : E];  // forward: bins of the owned output points
+    if constexpr (FWD && !LEAN) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             int j = t + T * e;
@@ -395,18 +458,25 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
         }
     }
 
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long cfirst = SPLIT ? (long long)cluster_index() : (long long)blockIdx.x;
+    const long long cstep = SPLIT ? (long long)cluster_count() : (long long)gridDim.x;
+    for (long long tile = cfirst; tile < ntiles; tile += cstep) {
         const long long f = tile * G + g;
         const bool valid = f < nfib;
         const long long o = valid ? f / inner : 0;
         const long long q = valid ? f - o * inner : 0;
         const long long base = o * (long long)n * inner + q;
 
-        R val[E];  // alpha (forward) or g (adjoint) at elements t + T e
+        R val[EV];  // alpha (forward) or g (adjoint) at elements t + T e (LEAN: in aux)
+        group_sync<T, G>(g);  // the previous tile is done with aux
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             int i = t + T * e;
-            val[e] = (valid && i < n) ? RealOps<R>::from_io(in[base + (long long)i * inner]) : RealOps<R>::zero();
+            R v = (valid && i < n) ? RealOps<R>::from_io(in[base + (long long)i * inner]) : RealOps<R>::zero();
+            if constexpr (LEAN)
+                aux[i] = v;
+            else
+                val[e] = v;
         }
         R acc[E];
 #pragma unroll
@@ -414,18 +484,24 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
 
         if constexpr (FWD) {
             // low-degree coefficients for the dense block, shared across the group
-            group_sync<T, G>(g);
+            if constexpr (!LEAN) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                int i = t + T * e;
-                if (i < nu0) aux[i] = val[e];
+                for (int e = 0; e < E; ++e) {
+                    int i = t + T * e;
+                    if (i < nu0) aux[i] = val[e];
+                }
             }
             group_sync<T, G>(g);
-            for (int k = 0; k < rank; ++k) {
+            for (int k = kb; k < ke; ++k) {
                 Cx<R> x[E];
                 const Cx<R>* vk = vtab + (size_t)k * L;
 #pragma unroll
-                for (int e = 0; e < E; ++e) x[e] = cscale(vk[t + T * e], val[e]);
+                for (int e = 0; e < E; ++e) {
+                    if constexpr (LEAN)
+                        x[e] = cscale(vk[t + T * e], aux[t + T * e]);
+                    else
+                        x[e] = cscale(vk[t + T * e], val[e]);
+                }
                 group_sync<T, G>(g);  // previous gather done with the buffer
                 fft<R, LOG2L>(x, sre, sim, tw, t, g);
                 group_sync<T, G>(g);  // last pass done reading the buffer
@@ -443,37 +519,34 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
                 for (int e = 0; e < E; ++e) {
                     int j = t + T * e;
                     if (j < n) {
-                        Cx<R> y{sre[S::pad(mj[e])], sim[S::pad(mj[e])]};
+                        const int m = LEAN ? __ldg(A.mtab + j) : mj[e];
+                        Cx<R> y{sre[S::pad(m)], sim[S::pad(m)]};
                         acc[e] = acc[e] + re_mul(uk[j], y);
                     }
                 }
             }
-            // dense block: acc_j += sum_{c < nu0} sqrt(w_j) P~_c(t_j) alpha_c
-            for (int c = 0; c < nu0; ++c) {
-                R ac = aux[c];
+            // dense block: acc_j += sum_{c < nu0} sqrt(w_j) P~_c(t_j) alpha_c (first CTA of a cluster)
+            if (!SPLIT || crank == 0) {
+                for (int c = 0; c < nu0; ++c) {
+                    R ac = aux[c];
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    int j = t + T * e;
-                    if (j < n) acc[e] = acc[e] + vblk[(size_t)c * n + j] * ac;
-                }
-            }
-            if (valid) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    int j = t + T * e;
-                    if (j < n) out[base + (long long)j * inner] = RealOps<R>::to_io(acc[e]);
+                    for (int e = 0; e < E; ++e) {
+                        int j = t + T * e;
+                        if (j < n) acc[e] = acc[e] + vblk[(size_t)c * n + j] * ac;
+                    }
                 }
             }
         } else {
             // adjoint: g of the fibre in shared memory for the bin scatter
-            group_sync<T, G>(g);
+            if constexpr (!LEAN) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                int j = t + T * e;
-                if (j < n) aux[j] = val[e];
+                for (int e = 0; e < E; ++e) {
+                    int j = t + T * e;
+                    if (j < n) aux[j] = val[e];
+                }
             }
             group_sync<T, G>(g);
-            for (int k = 0; k < rank; ++k) {
+            for (int k = kb; k < ke; ++k) {
                 const Cx<R>* uk = utab + (size_t)k * n;
                 Cx<R> x[E];
 #pragma unroll
@@ -496,27 +569,36 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
                 for (int e = 0; e < E; ++e) acc[e] = acc[e] + re_mul(vk[t + T * e], x[e]);
             }
             // dense block: alpha_c = sum_j sqrt(w_j) P~_c(t_j) g_j for c < nu0; the group
-            // reduces its partial sums through the FFT buffer
-            for (int c = 0; c < nu0; ++c) {
-                R part = RealOps<R>::zero();
+            // reduces its partial sums through the FFT buffer (first CTA of a cluster)
+            if (!SPLIT || crank == 0) {
+                for (int c = 0; c < nu0; ++c) {
+                    R part = RealOps<R>::zero();
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    int j = t + T * e;
-                    if (j < n) part = part + vblk[(size_t)c * n + j] * val[e];
-                }
-                group_sync<T, G>(g);
-                sre[t] = part;
-                group_sync<T, G>(g);
-                for (int s = T / 2; s > 0; s >>= 1) {
-                    if (t < s) sre[t] = sre[t] + sre[t + s];
+                    for (int e = 0; e < E; ++e) {
+                        int j = t + T * e;
+                        if (j < n) {
+                            if constexpr (LEAN)
+                                part = part + vblk[(size_t)c * n + j] * aux[j];
+                            else
+                                part = part + vblk[(size_t)c * n + j] * val[e];
+                        }
+                    }
                     group_sync<T, G>(g);
-                }
-                R tot = sre[0];
-                // element c is owned by thread c % T at e = c / T
+                    sre[t] = part;
+                    group_sync<T, G>(g);
+                    for (int s = T / 2; s > 0; s >>= 1) {
+                        if (t < s) sre[t] = sre[t] + sre[t + s];
+                        group_sync<T, G>(g);
+                    }
+                    R tot = sre[0];
+                    // element c is owned by thread c % T at e = c / T
 #pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (t + T * e == c) acc[e] = tot;
+                    for (int e = 0; e < E; ++e)
+                        if (t + T * e == c) acc[e] = tot;
+                }
             }
+        }
+        if (!SPLIT || csize == 1) {
             if (valid) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
@@ -524,6 +606,30 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
                     if (j < n) out[base + (long long)j * inner] = RealOps<R>::to_io(acc[e]);
                 }
             }
+        } else {
+            // partial sums of the cluster's CTAs: [G][L + 1] over the group buffers, then CTA
+            // crank adds up and stores its share of the tile's G x L elements
+            constexpr int LP = L + 1;
+            R* red = smem;
+            __syncthreads();  // every group is done with its buffers
+#pragma unroll
+            for (int e = 0; e < E; ++e) red[g * LP + t + T * e] = acc[e];
+            cluster_sync();
+            const int per = (G * L) / (int)csize;
+            for (int i = threadIdx.x; i < per; i += S::THREADS) {
+                const int el = (int)crank * per + i;
+                // strided axes: fibres fastest, so that neighbouring threads store neighbours
+                const int fib = (inner > 1) ? el % G : el / L;
+                const int j = (inner > 1) ? el / G : el % L;
+                const long long ff = tile * G + fib;
+                if (j < n && ff < nfib) {
+                    R v = RealOps<R>::zero();
+                    for (unsigned r = 0; r < csize; ++r) v = v + ld_cluster_r<R>(red + fib * LP + j, r);
+                    const long long oo = ff / inner, qq = ff - oo * inner;
+                    out[oo * (long long)n * inner + qq + (long long)j * inner] = RealOps<R>::to_io(v);
+                }
+            }
+            cluster_sync();  // the peers are done reading before the buffers are reused
         }
     }
 }

@@ -1,10 +1,18 @@
-// Double-word (hi + lo FP32) instances of the fused axis kernels (L = 1 .. 8192).
+// Double-word (hi + lo FP32) instances of the fused axis kernels (L = 1 .. 8192), no rank split.
 #include "jt_launch_impl.cuh"
 
 namespace jt {
+
 cudaError_t launch_axis_dw(const dev::AxisDev& A, int log2L, bool fwd, const double* in, double* out,
-                           long long nfib, long long inner, cudaStream_t s) {
+                           long long nfib, long long inner, int ksplit, cudaStream_t s) {
     if (log2L < 0 || log2L > MAX_LOG2L_DW) return cudaErrorInvalidValue;
-    return dispatch<dev::dw, MAX_LOG2L_DW>(log2L, A, fwd, in, out, nfib, inner, s);
+    if (ksplit > 1) return launch_axis_dw_split(A, log2L, fwd, in, out, nfib, inner, ksplit, s);
+    return generic_dispatch<dev::dw, MAX_LOG2L_DW, 0, false>(log2L, A, fwd, in, out, nfib, inner, 1, s);
 }
+
+int auto_ksplit_dw(int log2L, bool fwd, long long nfib, int rank) {
+    if (log2L < 0 || log2L > MAX_LOG2L_DW) return 1;
+    return generic_auto_ksplit<dev::dw, MAX_LOG2L_DW, 0>(log2L, fwd, nfib, rank);
+}
+
 }  // namespace jt

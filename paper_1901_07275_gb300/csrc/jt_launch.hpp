@@ -1,4 +1,5 @@
-// Launchers of the fused axis kernels, one translation unit per precision.
+// Launchers of the fused axis kernels.  Every launcher takes ksplit, the number of CTAs that
+// share a tile of fibres by splitting its rank terms (a thread-block cluster; 1 = no split).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,18 +10,32 @@
 namespace jt {
 
 // Apply one axis (forward or adjoint) to nfib fibres: fibre f = (o, q) with o = f / inner,
-// q = f % inner starts at o * n * inner + q and has stride inner.  in may equal out.
+// q = f % inner starts at o * n * inner + q and has stride inner.  in may equal out: a tile
+// stores only its own fibres, after all of its CTAs have read them.
 cudaError_t launch_axis_f32(const dev::AxisDev& A, int log2L, bool fwd, const float* in, float* out,
-                            long long nfib, long long inner, cudaStream_t s);
+                            long long nfib, long long inner, int ksplit, cudaStream_t s);
 cudaError_t launch_axis_dw(const dev::AxisDev& A, int log2L, bool fwd, const double* in, double* out,
-                           long long nfib, long long inner, cudaStream_t s);
+                           long long nfib, long long inner, int ksplit, cudaStream_t s);
+// rank-split instances (separate translation units)
+cudaError_t launch_axis_f32_split(const dev::AxisDev& A, int log2L, bool fwd, const float* in, float* out,
+                                  long long nfib, long long inner, int ksplit, cudaStream_t s);
+cudaError_t launch_axis_dw_split(const dev::AxisDev& A, int log2L, bool fwd, const double* in, double* out,
+                                 long long nfib, long long inner, int ksplit, cudaStream_t s);
 
 // One launch of the four-step kernel over the concatenated tiles of several jobs of the same
 // FFT length, direction and stride kind (jobs: a device array ordered by tile_begin).
 cudaError_t launch_axis_f32_batched(int log2L, bool fwd, bool strided, const dev::BatchJob* jobs, int njobs,
-                                    long long total_tiles, const dev::BatchPtrs& ptrs, cudaStream_t s);
+                                    long long total_tiles, const dev::BatchPtrs& ptrs, int ksplit, cudaStream_t s);
+cudaError_t launch_axis_f32_batched_split(int log2L, bool fwd, bool strided, const dev::BatchJob* jobs, int njobs,
+                                          long long total_tiles, const dev::BatchPtrs& ptrs, int ksplit,
+                                          cudaStream_t s);
 // Fibres per CTA tile of the four-step kernel (tile counting for batched jobs).
 int f32_warp_tile_fibres(int log2L);
+
+// The rank split a sweep of nfib fibres gets by default (1, 2, 4 or 8): CTAs per tile are
+// doubled while the split tiles still fit in one wave and every CTA keeps a rank term.
+int auto_ksplit_f32(int log2L, bool fwd, bool strided, long long nfib, int rank);
+int auto_ksplit_dw(int log2L, bool fwd, long long nfib, int rank);
 
 constexpr int MAX_LOG2L_F32 = 14;
 constexpr int MAX_LOG2L_DW = 13;

@@ -676,7 +676,7 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
                      const jt_options& opt) {
     if (n < 1 || n > 65536 || !valid_parameter(a) || !valid_parameter(b)) return JT_EINVAL;
     if (!(eps > 0.0 && eps < 1.0)) return JT_EINVAL;
-    if (opt.nu0 < 0 || opt.nu0 > 32 || opt.oversample_q < 1 || opt.rank_cap < 0 || opt.fft_len_policy != 0 || opt.autotune != 0)
+    if (opt.nu0 < 0 || opt.nu0 > 32 || opt.oversample_q < 1 || opt.rank_cap < 0 || opt.fft_len_policy != 0 || opt.autotune < 0 || opt.autotune > 1)
         return JT_EINVAL;
     if (points)
         for (int64_t k = 0; k < n; ++k)

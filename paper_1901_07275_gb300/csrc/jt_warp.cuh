@@ -126,7 +126,7 @@ struct BatchPtrs {
 // One forward or adjoint sweep over nfib fibres (see jt_axis.cuh for the operator).  With
 // BATCHED, the kernel walks the concatenated tiles of njobs jobs instead (same arithmetic;
 // the per-job constants are reloaded when a CTA moves on to the next job).
-template <int LOG2L, bool FWD, bool STRIDED, bool BATCHED = false>
+template <int LOG2L, bool FWD, bool STRIDED, bool BATCHED = false, bool SPLIT = false>
 __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     warp_axis_kernel(AxisDev A, const float* in, float* out, long long nfib, long long inner,
                      const BatchJob* __restrict__ jobs, int njobs, long long total_tiles, const __grid_constant__ BatchPtrs ptrs) {
@@ -188,7 +188,12 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     if constexpr (!BATCHED) load_job_constants();
 
     const long long ntiles = BATCHED ? total_tiles : (nfib + FT - 1) / FT;
-    for (long long g_tile = blockIdx.x; g_tile < ntiles; g_tile += gridDim.x) {
+    // rank split over the CTAs of a cluster (jt_axis.cuh); every CTA of a cluster walks the
+    // same tiles, so all of them meet the same cluster barriers
+    const unsigned csize = SPLIT ? cluster_size() : 1u, crank = SPLIT ? cluster_rank() : 0u;
+    const long long cfirst = SPLIT ? (long long)cluster_index() : (long long)blockIdx.x;
+    const long long cstep = SPLIT ? (long long)cluster_count() : (long long)gridDim.x;
+    for (long long g_tile = cfirst; g_tile < ntiles; g_tile += cstep) {
         long long tile_i = g_tile;
         if constexpr (BATCHED) {
             // jobs are ordered by tile_begin and a CTA's tiles increase: advance, or search once
@@ -268,7 +273,11 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         float* vres = reinterpret_cast<float*>(smem_raw);
         const float* __restrict__ auxbase =
             reinterpret_cast<const float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF);
-        if constexpr (FWD) {
+        if (SPLIT && crank != 0) {
+            // rank-split partners: the dense block belongs to the first CTA of the cluster
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[e] = 0.0f;
+        } else if constexpr (FWD) {
             // FT x L outputs, 16 per thread: JPT points x FPT fibres
             constexpr int JPT = (L > 256) ? L / 256 : 1;
             constexpr int FPT = 16 / JPT;
@@ -297,6 +306,61 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             __syncthreads();
 #pragma unroll
             for (int e = 0; e < 16; ++e) acc[e] = vres[fl * L + t + T * e];
+        } else if constexpr (FT <= 2) {
+            // alpha_c(fibre) = sum_j vblk[c][j] g_j with one or two fibres a tile (L >= 2048):
+            // every thread takes L/256 points of each fibre and all degrees, so that its table
+            // loads are independent of one another; a transposing butterfly leaves lane l of
+            // each warp with the warp's sum for degree l, and the warps' sums are added last.
+            constexpr int JPT = L / 256;
+            float* wpart = vres + 2 * FT * 32;  // [warp][FT][32]
+            float gv[FT][JPT];
+#pragma unroll
+            for (int ff = 0; ff < FT; ++ff)
+#pragma unroll
+                for (int jj = 0; jj < JPT; ++jj) gv[ff][jj] = auxbase[(size_t)ff * S::AUX + S::apad(threadIdx.x + 256 * jj)];
+            float part[FT][32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                float v[JPT];
+#pragma unroll
+                for (int jj = 0; jj < JPT; ++jj) v[jj] = (c < nu0) ? __ldg(vblk + (size_t)c * L + threadIdx.x + 256 * jj) : 0.0f;
+#pragma unroll
+                for (int ff = 0; ff < FT; ++ff) {
+                    float a = 0.0f;
+#pragma unroll
+                    for (int jj = 0; jj < JPT; ++jj) a = fmaf(v[jj], gv[ff][jj], a);
+                    part[ff][c] = a;
+                }
+            }
+#pragma unroll
+            for (int ff = 0; ff < FT; ++ff) {
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+                    const bool upper = (lane & off) != 0;
+#pragma unroll
+                    for (int i = 0; i < off; ++i) {
+                        const float send = upper ? part[ff][i] : part[ff][i + off];
+                        const float keep = upper ? part[ff][i + off] : part[ff][i];
+                        part[ff][i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                    }
+                }
+                wpart[(warp * FT + ff) * 32 + lane] = part[ff][0];
+            }
+            __syncthreads();
+            if (threadIdx.x < FT * 32) {
+                const int ff = threadIdx.x >> 5, c = threadIdx.x & 31;
+                float tot = 0.0f;
+#pragma unroll
+                for (int w = 0; w < S::WARPS; ++w) tot += wpart[(w * FT + ff) * 32 + c];
+                vres[ff * 32 + c] = tot;
+                vres[(FT + ff) * 32 + c] = 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < 16; ++o) {
+                const int nu = Own<LOG2L, FWD>::idx(t, o);
+                acc[o] = (nu < nu0) ? vres[fl * 32 + nu] : 0.0f;
+            }
         } else {
             // alpha_c(fibre) = sum_j vblk[c][j] g_j: warp w takes (fibre chunk, degree) items,
             // lanes split the points, partials for 8 fibres at a time, then a warp sum
@@ -346,7 +410,9 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             }
         }
 
-        for (int k = 0; k < rank; ++k) {
+        const int kb = (int)(((long long)rank * crank) / csize);
+        const int ke = (int)(((long long)rank * (crank + 1)) / csize);
+        for (int k = kb; k < ke; ++k) {
             Cx<float> x[16];
             if constexpr (FWD) {
                 const float2* vk = vtab + (size_t)k * L;
@@ -511,7 +577,36 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         }
 
         // store
-        if constexpr (STRIDED) {
+        if (SPLIT && csize > 1) {
+            // partial sums of the cluster's CTAs, [FT][L + 1] over the exchange region; CTA
+            // crank adds up and stores its share of the tile's FT x L = 4096 elements
+            constexpr int LP = L + 1;
+            float* red = reinterpret_cast<float*>(smem_raw);
+            __syncthreads();  // every group is done with the exchange region
+            if constexpr (FWD) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) red[fl * LP + t + T * e] = acc[e];
+            } else {
+#pragma unroll
+                for (int o = 0; o < 16; ++o) red[fl * LP + Own<LOG2L, FWD>::idx(t, o)] = acc[o];
+            }
+            cluster_sync();
+            const int per = (FT * L) / (int)csize;
+            for (int i = threadIdx.x; i < per; i += S::THREADS) {
+                const int el = (int)crank * per + i;
+                // strided axes: fibres fastest, so that neighbouring threads store neighbours
+                const int fib = STRIDED ? el % FT : el / L;
+                const int j = STRIDED ? el / FT : el % L;
+                const long long ff = f0 + fib;
+                if (j < n && ff < nfib) {
+                    float v = 0.0f;
+                    for (unsigned r = 0; r < csize; ++r) v += ld_cluster(red + fib * LP + j, r);
+                    const long long oo = ff / inner, qq = ff - oo * inner;
+                    out[oo * (long long)n * inner + qq + (long long)j * inner] = v;
+                }
+            }
+            cluster_sync();  // the peers are done reading before the region is reused
+        } else if constexpr (STRIDED) {
             __syncthreads();
             if constexpr (FWD) {
 #pragma unroll

@@ -22,7 +22,7 @@ class Transform:
     """
 
     def __init__(self, n, a, b, points=None, eps=None, precision="fp32", nu0=27, rank_cap=0,
-                 oversample_q=3, seed=None, stream=None):
+                 oversample_q=3, seed=None, autotune=False, stream=None):
         import torch
 
         self.n = tuple(int(v) for v in n)
@@ -33,7 +33,8 @@ class Transform:
         self.eps = _DEFAULT_EPS[precision] if eps is None else float(eps)
         self.dtype = getattr(torch, _DTYPES[precision])
         self.uniform = points is None or all(p is None for p in points)
-        opt = B.options(precision, nu0=nu0, rank_cap=rank_cap, oversample_q=oversample_q, seed=seed)
+        opt = B.options(precision, nu0=nu0, rank_cap=rank_cap, oversample_q=oversample_q, seed=seed,
+                        autotune=1 if autotune else 0)
         s = self._stream(stream)
         self._plan = B.jt_plan_create(self.n, self.a, self.b, points, self.eps, opt, s)
         self.info = [B.jt_plan_info(self._plan, i, self.n[i]) for i in range(self.d)]
@@ -53,6 +54,18 @@ class Transform:
     @property
     def fft_lens(self):
         return [i["fft_len"] for i in self.info]
+
+    def set_ksplit(self, ksplit, axis=-1, direction=-1):
+        """Fix the rank split (CTAs sharing a tile: 1, 2, 4, 8; 0 = occupancy rule)."""
+        B.jt_plan_set_ksplit(self._plan, axis, direction, ksplit)
+
+    def tune(self, nrhs, stream=None):
+        """Measure and keep the fastest rank split of every sweep for ``nrhs`` right-hand sides."""
+        B.jt_plan_tune(self._plan, nrhs, self._stream(stream))
+
+    def schedule(self, axis, direction, nrhs):
+        """Rank split of the sweep of ``axis`` in ``direction`` (0 forward, 1 adjoint)."""
+        return B.jt_plan_schedule(self._plan, axis, direction, nrhs)
 
     def nodes(self, axis):
         return self.info[axis]["t"]
