@@ -108,6 +108,31 @@ struct Own {
     }
 };
 
+// Sum CNT values per lane over the lanes of a group (xor offsets OFF, OFF/2, .., 1) so that
+// each lane keeps a share: at every step the lanes with that offset bit set keep the upper
+// half of their live values and add the partner's copy of it, so after log2(CNT) steps lane u
+// holds the total of output base(u) (further steps, if any, are plain pairwise sums).
+template <int OFF, int CNT>
+__device__ __forceinline__ void transpose_reduce(float* v, int u, int& base) {
+    if constexpr (OFF >= 1) {
+        if constexpr (CNT > 1) {
+            constexpr int H = CNT / 2;
+            const bool upper = (u & OFF) != 0;
+#pragma unroll
+            for (int i = 0; i < H; ++i) {
+                const float send = upper ? v[i] : v[i + H];
+                const float keep = upper ? v[i + H] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+            }
+            if (upper) base += H;
+            transpose_reduce<OFF / 2, H>(v, u, base);
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], OFF);
+            transpose_reduce<OFF / 2, 1>(v, u, base);
+        }
+    }
+}
+
 // One sweep of one axis of one transform, as an entry of a batched launch: the CTA tiles of
 // all jobs of a launch are numbered consecutively, job i owning [tile_begin, tile_begin + tiles).
 // The job tables are built once per batch; the caller's array pointers of one launch travel as
@@ -362,40 +387,56 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 acc[o] = (nu < nu0) ? vres[fl * 32 + nu] : 0.0f;
             }
         } else {
-            // alpha_c(fibre) = sum_j vblk[c][j] g_j: warp w takes (fibre chunk, degree) items,
-            // lanes split the points, partials for 8 fibres at a time, then a warp sum
-            constexpr int NCH = (FT + 7) / 8;
-            constexpr int HALF = L / 2;  // items cover half of the points each, for balance
-            for (int item = warp; item < 2 * NCH * nu0; item += S::WARPS) {
-                const int half = item & 1, ch = (item >> 1) / nu0, c = (item >> 1) % nu0;
-                float part[8];
+            // alpha_c(fibre) = sum_j vblk[c][j] g_j with FT >= 4 fibres a tile, as a register-
+            // blocked product: block (cb, fb) = degrees 4 cb .. 4 cb + 3 x fibres FB fb ..
+            // FB fb + FB - 1 is owned by TPB consecutive lanes, lane u taking the points
+            // j = u + TPB q; a transposing butterfly then sums each output over the TPB lanes.
+            constexpr int CB = 4;
+            constexpr int FB = (FT >= 256) ? 8 : 4;
+            constexpr int NV = CB * FB;
+            constexpr int NBLK = (32 / CB) * (FT / FB);
+            constexpr int TPB = S::THREADS / NBLK;  // 1 .. 32
+            constexpr int JR = L / TPB;
+            static_assert(TPB >= 1 && TPB <= 32 && NBLK * TPB == S::THREADS, "dense-block blocking");
+            const int blk = threadIdx.x / TPB, u = threadIdx.x % TPB;
+            const int cb = blk % (32 / CB), fb = blk / (32 / CB);
+            float v[NV];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) part[i] = 0.0f;
+            for (int i = 0; i < NV; ++i) v[i] = 0.0f;
+            bool crow[CB];
 #pragma unroll
-                for (int j = half * HALF + lane; j < (half + 1) * HALF; j += 32) {
-                    const float v = __ldg(vblk + (size_t)c * L + j);
+            for (int i = 0; i < CB; ++i) crow[i] = CB * cb + i < nu0;
+#pragma unroll 8
+            for (int q = 0; q < JR; ++q) {
+                const int j = u + TPB * q;
+                float vv[CB], gg[FB];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int ff = ch * 8 + i;
-                        if (ff < FT) part[i] = fmaf(v, auxbase[(size_t)ff * S::AUX + S::apad(j)], part[i]);
-                    }
-                }
+                for (int i = 0; i < CB; ++i) vv[i] = crow[i] ? __ldg(vblk + (size_t)(CB * cb + i) * L + j) : 0.0f;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int f = 0; f < FB; ++f) gg[f] = auxbase[(size_t)(FB * fb + f) * S::AUX + S::apad(j)];
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) part[i] += __shfl_xor_sync(0xffffffffu, part[i], off);
-                }
-                if (lane == 0) {
+                for (int i = 0; i < CB; ++i)
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (ch * 8 + i < FT) vres[(half * FT + ch * 8 + i) * 32 + c] = part[i];
+                    for (int f = 0; f < FB; ++f) v[i * FB + f] = fmaf(vv[i], gg[f], v[i * FB + f]);
+            }
+            // lane u ends with outputs base .. base + NV/TPB - 1 (TPB > NV: duplicated on lanes
+            // that differ in the low bits; the one with those bits clear stores)
+            int base = 0;
+            transpose_reduce<TPB / 2, NV>(v, u, base);
+            constexpr int KEEP = (NV / TPB > 0) ? NV / TPB : 1;
+            constexpr int DUP = (TPB > NV) ? TPB / NV - 1 : 0;
+            if ((u & DUP) == 0) {
+#pragma unroll
+                for (int i = 0; i < KEEP; ++i) {
+                    const int o = base + i;
+                    vres[(FB * fb + o % FB) * 32 + CB * cb + o / FB] = v[i];
                 }
             }
             __syncthreads();
 #pragma unroll
             for (int o = 0; o < 16; ++o) {
                 const int nu = Own<LOG2L, FWD>::idx(t, o);
-                acc[o] = (nu < nu0) ? vres[fl * 32 + nu] + vres[(FT + fl) * 32 + nu] : 0.0f;
+                acc[o] = (nu < nu0) ? vres[fl * 32 + nu] : 0.0f;
             }
         }
         __syncthreads();  // results read before the rank loop reuses the exchange region
