@@ -61,6 +61,18 @@ struct WShape {
     }
 };
 
+// Element offset of fibre f = (o, q), o = f / inner, q = f % inner, of an array whose axis of
+// length n has stride inner: o n inner + q.  32-bit division when the operands allow it.
+__device__ __forceinline__ long long fibre_offset(long long f, int n, long long inner) {
+    if (((unsigned long long)f | (unsigned long long)inner) < 0x100000000ull) {
+        const unsigned o = (unsigned)f / (unsigned)inner;
+        const unsigned q = (unsigned)f - o * (unsigned)inner;
+        return (long long)o * ((long long)n * inner) + q;
+    }
+    const long long o = f / inner;
+    return o * ((long long)n * inner) + (f - o * inner);
+}
+
 // Synchronise the T lanes of one fibre group (a warp or less, one CTA, or a named barrier).
 template <int T, int FT>
 __device__ __forceinline__ void gsync(int fl) {
@@ -157,6 +169,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                      const BatchJob* __restrict__ jobs, int njobs, long long total_tiles, const __grid_constant__ BatchPtrs ptrs) {
     using S = WShape<LOG2L>;
     constexpr int L = S::L, T = S::T, FT = S::FT;
+    constexpr bool VAL_SMEM = FWD && T >= 64;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fl = threadIdx.x / T;  // fibre slot in the CTA tile
@@ -250,16 +263,21 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         if constexpr (STRIDED) {
             __syncthreads();  // previous tile's stores done with the tile buffer
             {
-                // FT divides the CTA size, so each thread always serves the same fibre ql
+                // FT divides the CTA size, so each thread always serves the same fibre ql and
+                // walks its rows with a pointer increment
                 const int ql = threadIdx.x % FT;
                 const long long ff = f0 + ql;
-                long long gbase = 0;
+                constexpr int RSTEP = S::THREADS / FT;
+                const int r0 = threadIdx.x / FT;
+                float* trow = tile + ql * S::TROW;
                 if (ff < nfib) {
-                    const long long o = ff / inner, q = ff - o * inner;
-                    gbase = o * (long long)n * inner + q;
+                    const float* p = in + fibre_offset(ff, n, inner) + (long long)r0 * inner;
+                    const long long step = (long long)RSTEP * inner;
+#pragma unroll 4
+                    for (int row = r0; row < n; row += RSTEP, p += step) trow[row] = *p;
+                } else {
+                    for (int row = r0; row < n; row += RSTEP) trow[row] = 0.0f;
                 }
-                for (int row = threadIdx.x / FT; row < n; row += S::THREADS / FT)
-                    tile[ql * S::TROW + row] = (ff < nfib) ? in[gbase + (long long)row * inner] : 0.0f;
             }
             __syncthreads();
 #pragma unroll
@@ -279,10 +297,12 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         float acc[16];
         __syncthreads();  // the previous tile is done with aux and the exchange region
         if constexpr (FWD) {
+            // lengths L >= 1024 keep the whole fibre here instead of in registers (it is
+            // re-read by every rank term), which leaves room for the two-level step B
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 int p = t + T * s;
-                if (p < nu0) aux[p] = val[s];
+                if (VAL_SMEM || p < nu0) aux[p] = val[s];
             }
         } else {
 #pragma unroll
@@ -460,7 +480,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
                     float2 v = __ldg(vk + t + T * s);
-                    x[s] = Cx<float>{v.x * val[s], v.y * val[s]};
+                    const float a = VAL_SMEM ? aux[t + T * s] : val[s];
+                    x[s] = Cx<float>{v.x * a, v.y * a};
                 }
             } else {
                 // z[m] = sum_{j : m_j = m} u_k[j] g_j for the owned bins m = t + T s; only
@@ -642,8 +663,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 if (j < n && ff < nfib) {
                     float v = 0.0f;
                     for (unsigned r = 0; r < csize; ++r) v += ld_cluster(red + fib * LP + j, r);
-                    const long long oo = ff / inner, qq = ff - oo * inner;
-                    out[oo * (long long)n * inner + qq + (long long)j * inner] = v;
+                    out[fibre_offset(ff, n, inner) + (long long)j * inner] = v;
                 }
             }
             cluster_sync();  // the peers are done reading before the region is reused
@@ -667,10 +687,13 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 const int ql = threadIdx.x % FT;
                 const long long ff = f0 + ql;
                 if (ff < nfib) {
-                    const long long o = ff / inner, q = ff - o * inner;
-                    const long long gbase = o * (long long)n * inner + q;
-                    for (int row = threadIdx.x / FT; row < n; row += S::THREADS / FT)
-                        out[gbase + (long long)row * inner] = tile[ql * S::TROW + row];
+                    constexpr int RSTEP = S::THREADS / FT;
+                    const int r0 = threadIdx.x / FT;
+                    const float* trow = tile + ql * S::TROW;
+                    float* p = out + fibre_offset(ff, n, inner) + (long long)r0 * inner;
+                    const long long step = (long long)RSTEP * inner;
+#pragma unroll 4
+                    for (int row = r0; row < n; row += RSTEP, p += step) *p = trow[row];
                 }
             }
         } else if (valid) {
