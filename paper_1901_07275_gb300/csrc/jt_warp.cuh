@@ -85,13 +85,28 @@ __device__ __forceinline__ void gsync(int fl) {
     }
 }
 
+// Input staging buffers: two (the next tile's input is fetched during this tile's rank
+// terms) unless that would leave room for only one CTA an SM.
+template <int LOG2L>
+constexpr int warp_nstage() {
+    using S = WShape<LOG2L>;
+    return ((size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + 2 * (size_t)S::FT * S::TROW * 4 <= 112 * 1024) ? 2 : 1;
+}
 template <int LOG2L>
 constexpr size_t warp_smem_bytes(bool strided) {
     using S = WShape<LOG2L>;
-    size_t b = (size_t)S::FT * (S::BUF * 8 + S::AUX * 4);
-    if (strided) b += (size_t)S::FT * S::TROW * 4;
-    return b;
+    (void)strided;
+    return (size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)warp_nstage<LOG2L>() * S::FT * S::TROW * 4;
 }
+
+// Asynchronous 4-byte global -> shared copy (zero-filled when !valid; src must still be a
+// mapped address), and the group commit / wait of the issuing thread.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ float2 f2(Cx<float> c) { return make_float2(c.re, c.im); }
 __device__ __forceinline__ Cx<float> cx(float2 v) { return Cx<float>{v.x, v.y}; }
@@ -176,7 +191,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     const int t = threadIdx.x % T;
     float2* buf = reinterpret_cast<float2*>(smem_raw) + (size_t)fl * S::BUF;
     float* aux = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)fl * S::AUX;
-    float* tile = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)FT * S::AUX;
+    // two staging buffers of FT x TROW floats (input of this tile and of the next one)
+    float* stage = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)FT * S::AUX;
 
     if constexpr (BATCHED) {
         if (njobs <= 0) return;
@@ -231,20 +247,75 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     const unsigned csize = SPLIT ? cluster_size() : 1u, crank = SPLIT ? cluster_rank() : 0u;
     const long long cfirst = SPLIT ? (long long)cluster_index() : (long long)blockIdx.x;
     const long long cstep = SPLIT ? (long long)cluster_count() : (long long)gridDim.x;
-    for (long long g_tile = cfirst; g_tile < ntiles; g_tile += cstep) {
+
+    // Batched launches: the job of global tile gt (jobs are ordered by tile_begin and a CTA's
+    // tiles increase, so a hint from an earlier tile only moves forward).
+    auto find_job = [&](long long gt, int hint) -> int {
+        int j = hint;
+        if (j < 0) {
+            int lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].tile_begin <= gt) lo = mid; else hi = mid - 1;
+            }
+            j = lo;
+        }
+        while (j + 1 < njobs && jobs[j + 1].tile_begin <= gt) ++j;
+        return j;
+    };
+    // Stage the input of global tile gt into dst ([FT][TROW]) with asynchronous copies, so
+    // that the next tile's input arrives while this tile's rank terms run.  Contiguous
+    // fibres: each thread copies the elements t + T s of its own fibre (and later reads back
+    // only those); strided fibres: thread (ql, r0) walks rows r0, r0 + RSTEP, .. of fibre ql.
+    int pf_job = -1;
+    auto stage_tile = [&](long long gt, float* dst) {
+        const float* src = in;
+        long long nf = nfib, inr = inner, ti = gt;
+        int nn = n;
+        if constexpr (BATCHED) {
+            pf_job = find_job(gt, pf_job);
+            const BatchJob& J = jobs[pf_job];
+            src = ptrs.in[J.slot];
+            nf = J.nfib;
+            inr = J.inner;
+            nn = J.A.n;
+            ti = gt - J.tile_begin;
+        }
+        const long long g0 = ti * FT;
+        if constexpr (STRIDED) {
+            const int ql = threadIdx.x % FT;
+            const long long ff = g0 + ql;
+            constexpr int RSTEP = S::THREADS / FT;
+            const int r0 = threadIdx.x / FT;
+            float* trow = dst + ql * S::TROW;
+            if (ff < nf) {
+                const float* p = src + fibre_offset(ff, nn, inr) + (long long)r0 * inr;
+                const long long step = (long long)RSTEP * inr;
+#pragma unroll 4
+                for (int row = r0; row < nn; row += RSTEP, p += step) cp_async4(trow + row, p, true);
+            } else {
+                for (int row = r0; row < nn; row += RSTEP) cp_async4(trow + row, src, false);
+            }
+        } else {
+            const long long ff = g0 + fl;
+            const bool ok = ff < nf;
+            const float* p = src + (ok ? ff * (long long)nn : 0);
+#pragma unroll
+            for (int s2 = 0; s2 < 16; ++s2) {
+                const int q = t + T * s2;
+                if (q < nn) cp_async4(dst + fl * S::TROW + q, p + q, ok);
+            }
+        }
+        cp_async_commit();
+    };
+
+    constexpr int NSTAGE = warp_nstage<LOG2L>();
+    int cur = 0;
+    if (NSTAGE == 2 && cfirst < ntiles) stage_tile(cfirst, stage);
+    for (long long g_tile = cfirst; g_tile < ntiles; g_tile += cstep, cur ^= (NSTAGE - 1)) {
         long long tile_i = g_tile;
         if constexpr (BATCHED) {
-            // jobs are ordered by tile_begin and a CTA's tiles increase: advance, or search once
-            int j = cur_job < 0 ? 0 : cur_job;
-            if (cur_job < 0) {
-                int lo = 0, hi = njobs - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (jobs[mid].tile_begin <= g_tile) lo = mid; else hi = mid - 1;
-                }
-                j = lo;
-            }
-            while (j + 1 < njobs && jobs[j + 1].tile_begin <= g_tile) ++j;
+            const int j = find_job(g_tile, cur_job);
             if (j != cur_job) {
                 A = jobs[j].A;
                 in = ptrs.in[jobs[j].slot];
@@ -259,40 +330,23 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         const long long f0 = tile_i * FT;
         const long long f = f0 + fl;
         const bool valid = f < nfib;
-        float val[16];
-        if constexpr (STRIDED) {
-            __syncthreads();  // previous tile's stores done with the tile buffer
-            {
-                // FT divides the CTA size, so each thread always serves the same fibre ql and
-                // walks its rows with a pointer increment
-                const int ql = threadIdx.x % FT;
-                const long long ff = f0 + ql;
-                constexpr int RSTEP = S::THREADS / FT;
-                const int r0 = threadIdx.x / FT;
-                float* trow = tile + ql * S::TROW;
-                if (ff < nfib) {
-                    const float* p = in + fibre_offset(ff, n, inner) + (long long)r0 * inner;
-                    const long long step = (long long)RSTEP * inner;
-#pragma unroll 4
-                    for (int row = r0; row < n; row += RSTEP, p += step) trow[row] = *p;
-                } else {
-                    for (int row = r0; row < n; row += RSTEP) trow[row] = 0.0f;
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                int p = t + T * s;
-                val[s] = (p < n) ? tile[fl * S::TROW + p] : 0.0f;
-            }
-        } else {
-            const long long base = f * (long long)n;
-#pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                int p = t + T * s;
-                val[s] = (valid && p < n) ? in[base + p] : 0.0f;
-            }
+        float* tile = stage + cur * (FT * S::TROW);
+        if constexpr (NSTAGE == 1) {
+            if constexpr (STRIDED) __syncthreads();  // the previous tile's output transpose is done
+            stage_tile(g_tile, tile);
         }
+        cp_async_wait_all();
+        if constexpr (STRIDED) __syncthreads();  // rows staged by other threads
+        float val[16];
+#pragma unroll
+        for (int s2 = 0; s2 < 16; ++s2) {
+            const int p = t + T * s2;
+            val[s2] = (p < n) ? tile[fl * S::TROW + p] : 0.0f;
+        }
+        // The other buffer was last read by the previous tile: contiguous fibres only by the
+        // thread that staged each element, strided ones (input and output transpose) before
+        // the barrier above.
+        if (NSTAGE == 2 && g_tile + cstep < ntiles) stage_tile(g_tile + cstep, stage + (cur ^ 1) * (FT * S::TROW));
 
         float acc[16];
         __syncthreads();  // the previous tile is done with aux and the exchange region
@@ -305,11 +359,10 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 if (VAL_SMEM || p < nu0) aux[p] = val[s];
             }
         } else {
+            // all L points, zero beyond n: the dense block multiplies the zero-padded table
+            // rows by every entry, so none may be left unwritten
 #pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                int p = t + T * s;
-                if (p < n) aux[S::apad(p)] = val[s];
-            }
+            for (int s = 0; s < 16; ++s) aux[S::apad(t + T * s)] = val[s];
         }
         __syncthreads();
         // Dense low-degree block for the whole tile at once, so that each row of the table
