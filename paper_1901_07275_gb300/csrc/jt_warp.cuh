@@ -87,16 +87,18 @@ __device__ __forceinline__ void gsync(int fl) {
 
 // Input staging buffers: two (the next tile's input is fetched during this tile's rank
 // terms) unless that would leave room for only one CTA an SM.
-template <int LOG2L>
+// Contiguous fibres are loaded straight into registers and need none.
+template <int LOG2L, bool STRIDED>
 constexpr int warp_nstage() {
     using S = WShape<LOG2L>;
+    if (!STRIDED) return 0;
     return ((size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + 2 * (size_t)S::FT * S::TROW * 4 <= 112 * 1024) ? 2 : 1;
 }
 template <int LOG2L>
 constexpr size_t warp_smem_bytes(bool strided) {
     using S = WShape<LOG2L>;
-    (void)strided;
-    return (size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)warp_nstage<LOG2L>() * S::FT * S::TROW * 4;
+    const int ns = strided ? warp_nstage<LOG2L, true>() : 0;
+    return (size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)ns * S::FT * S::TROW * 4;
 }
 
 // Asynchronous 4-byte global -> shared copy (zero-filled when !valid; src must still be a
@@ -263,10 +265,9 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         while (j + 1 < njobs && jobs[j + 1].tile_begin <= gt) ++j;
         return j;
     };
-    // Stage the input of global tile gt into dst ([FT][TROW]) with asynchronous copies, so
-    // that the next tile's input arrives while this tile's rank terms run.  Contiguous
-    // fibres: each thread copies the elements t + T s of its own fibre (and later reads back
-    // only those); strided fibres: thread (ql, r0) walks rows r0, r0 + RSTEP, .. of fibre ql.
+    // Strided axes: stage the input of global tile gt into dst ([FT][TROW]) with asynchronous
+    // copies, so that the next tile's input arrives while this tile's rank terms run; thread
+    // (ql, r0) walks rows r0, r0 + RSTEP, .. of fibre ql.
     int pf_job = -1;
     auto stage_tile = [&](long long gt, float* dst) {
         const float* src = in;
@@ -296,20 +297,11 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             } else {
                 for (int row = r0; row < nn; row += RSTEP) cp_async4(trow + row, src, false);
             }
-        } else {
-            const long long ff = g0 + fl;
-            const bool ok = ff < nf;
-            const float* p = src + (ok ? ff * (long long)nn : 0);
-#pragma unroll
-            for (int s2 = 0; s2 < 16; ++s2) {
-                const int q = t + T * s2;
-                if (q < nn) cp_async4(dst + fl * S::TROW + q, p + q, ok);
-            }
         }
         cp_async_commit();
     };
 
-    constexpr int NSTAGE = warp_nstage<LOG2L>();
+    constexpr int NSTAGE = warp_nstage<LOG2L, STRIDED>();
     int cur = 0;
     if (NSTAGE == 2 && cfirst < ntiles) stage_tile(cfirst, stage);
     for (long long g_tile = cfirst; g_tile < ntiles; g_tile += cstep, cur ^= (NSTAGE - 1)) {
@@ -331,22 +323,30 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         const long long f = f0 + fl;
         const bool valid = f < nfib;
         float* tile = stage + cur * (FT * S::TROW);
-        if constexpr (NSTAGE == 1) {
-            if constexpr (STRIDED) __syncthreads();  // the previous tile's output transpose is done
-            stage_tile(g_tile, tile);
-        }
-        cp_async_wait_all();
-        if constexpr (STRIDED) __syncthreads();  // rows staged by other threads
         float val[16];
+        if constexpr (STRIDED) {
+            if constexpr (NSTAGE == 1) {
+                __syncthreads();  // the previous tile's output transpose is done
+                stage_tile(g_tile, tile);
+            }
+            cp_async_wait_all();
+            __syncthreads();  // rows staged by other threads
 #pragma unroll
-        for (int s2 = 0; s2 < 16; ++s2) {
-            const int p = t + T * s2;
-            val[s2] = (p < n) ? tile[fl * S::TROW + p] : 0.0f;
+            for (int s2 = 0; s2 < 16; ++s2) {
+                const int p = t + T * s2;
+                val[s2] = (p < n) ? tile[fl * S::TROW + p] : 0.0f;
+            }
+            // the other buffer was last read by the previous tile (input and output
+            // transpose), before the barrier above
+            if (NSTAGE == 2 && g_tile + cstep < ntiles) stage_tile(g_tile + cstep, stage + (cur ^ 1) * (FT * S::TROW));
+        } else {
+            const long long base = f * (long long)n;
+#pragma unroll
+            for (int s2 = 0; s2 < 16; ++s2) {
+                const int p = t + T * s2;
+                val[s2] = (valid && p < n) ? in[base + p] : 0.0f;
+            }
         }
-        // The other buffer was last read by the previous tile: contiguous fibres only by the
-        // thread that staged each element, strided ones (input and output transpose) before
-        // the barrier above.
-        if (NSTAGE == 2 && g_tile + cstep < ntiles) stage_tile(g_tile + cstep, stage + (cur ^ 1) * (FT * S::TROW));
 
         float acc[16];
         __syncthreads();  // the previous tile is done with aux and the exchange region
