@@ -255,6 +255,8 @@ def other_configs(dev, stream):
 
     out = {}
     cases = [
+        ("1d-1024 x 1 rhs", "1d-1024", 1),
+        ("1d-1024 x 256 rhs", "1d-1024", 256),
         ("1d-1024 x 8192 rhs", "1d-1024", 8192),
         ("3d-256", "3d-256", 1),
         ("2d-nonuniform-1024 x 16 rhs (forward + adjoint)", "2d-nonuniform-1024", 16),
@@ -266,21 +268,36 @@ def other_configs(dev, stream):
         f = torch.empty_like(x)
         y = torch.empty_like(x)
         back = T.inverse if T.uniform else T.adjoint
-        for _ in range(2):
+
+        def step():
             T.forward(x, out=f)
             back(f, out=y)
+
+        for _ in range(2):
+            step()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # small cases: enough steps for about 20 ms of timed work
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(3):
-            T.forward(x, out=f)
-            back(f, out=y)
+        step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 3
+        reps = int(min(2000, max(3, 20.0 / max(e0.elapsed_time(e1), 1e-3))))
+        e0.record(stream)
+        for _ in range(reps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
         coeffs = 2 * x.numel()
-        out[label] = {"coeffs_per_s": coeffs / (ms * 1e-3), "ms_per_step": ms, "ranks": T.ranks,
-                      "fft_len": T.fft_lens}
+        total = x.numel()
+        flops = 0.0
+        for ax, m in enumerate(w["n"]):
+            flops += 2 * (total // m) * axis_flops(m, T.fft_lens[ax], T.ranks[ax])
+        out[label] = {"coeffs_per_s": coeffs / (ms * 1e-3), "ms_per_step": ms, "steps_timed": reps,
+                      "ranks": T.ranks, "fft_len": T.fft_lens,
+                      "rank_split": [T.schedule(a, 0, nr) for a in range(len(w["n"]))],
+                      "algorithmic_tflops": flops / (ms * 1e-3) / 1e12}
         T.close()
         del x, f, y
     return out
