@@ -20,6 +20,10 @@ checkable reference:
   their d-dimensional tensor products (Sec. 3.2--3.3, Eqs. ``eq:2Djac``,
   ``eq:3Djac``) applied by dense mode products.
 
+The second-kind functions ``Q~`` (Sec. 1, Eq. ``eq:jacnonosci2``) for the second-kind
+transform are in ``second_kind.py``: the Stieltjes transform of the weight by adaptive
+quadrature and the same three-term recurrence under the principal-value integral.
+
 Recurrences and Newton iterations run in ``numpy.longdouble`` (80-bit extended
 on x86-64, IEEE binary128 on aarch64); dense summations run in float64.
 Every function is pinned by ``tests/test_oracle_pins.py`` against closed forms,
@@ -39,4 +43,13 @@ from .jacobi import (  # noqa: F401
     forward,
     adjoint,
     forward_sampled,
+)
+from .second_kind import (  # noqa: F401
+    stieltjes,
+    stieltjes_t,
+    second_kind_h,
+    modified_second_kind,
+    uniform_matrix_q,
+    nonuniform_matrix_q,
+    axis_matrix_q,
 )
