@@ -72,7 +72,19 @@ typedef struct {
     int32_t autotune;       /* 0: rank splits by the occupancy rule (see jt_plan_set_ksplit);
                                1: jt_batch_create measures them for every member sweep
                                (as jt_plan_tune does) before building the batch */
+    int32_t kind;           /* JT_FIRST_KIND (default) or JT_SECOND_KIND */
 } jt_options;
+
+/* Which modified Jacobi functions the transform expands in (Sec. 1, Eqs. eq:jacnonosci,
+ * eq:jacnonosci2; the paper notes the transform for Q~ is similar, Sec. 3.1--3.3):
+ *   JT_FIRST_KIND   P~_j = M cos(psi)  (the matrix J of every entry point above);
+ *   JT_SECOND_KIND  Q~_j = M sin(psi) = -(2/pi) C_j Q_j(cos t) sin(t/2)^{a+1/2} cos(t/2)^{b+1/2},
+ *                   Q_j the Jacobi function of the second kind on the cut (Szego 4.62), i.e. the
+ *                   imaginary part of the same B o F (Eq. eq:B): A_i = W_i Jq_i (Gauss--Jacobi
+ *                   nodes, same weights) or Jq_i (caller's angles).  Forward and adjoint only:
+ *                   Jq is not orthogonal, so jt_inverse returns JT_ENOTSUP; JT_FP64_PLAIN
+ *                   plans of the second kind are JT_ENOTSUP. */
+typedef enum { JT_FIRST_KIND = 0, JT_SECOND_KIND = 1 } jt_kind;
 
 /* Fill *opt with the defaults listed above. */
 void jt_options_default(jt_options* opt);

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libjt.so")
 
 JT_OK, JT_EINVAL, JT_ENOMEM, JT_ENOTSUP, JT_ECUDA, JT_ETIMEOUT, JT_ENOCONV = range(7)
 JT_FP32, JT_SPLIT, JT_FP64_PLAIN = 0, 1, 2
+JT_FIRST_KIND, JT_SECOND_KIND = 0, 1
+KINDS = {"first": JT_FIRST_KIND, "second": JT_SECOND_KIND}
 PRECISIONS = {"fp32": JT_FP32, "split": JT_SPLIT, "fp64_plain": JT_FP64_PLAIN}
 
 # every symbol declared in include/jt.h
@@ -60,6 +62,7 @@ class Options(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("fft_len_policy", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("kind", ctypes.c_int32),
     ]
 
 
@@ -129,7 +132,7 @@ def _check(status: int, what: str):
         raise JTError(status, what)
 
 
-def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None, autotune=0) -> Options:
+def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None, autotune=0, kind="first") -> Options:
     o = Options()
     lib().jt_options_default(ctypes.byref(o))
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
@@ -137,6 +140,7 @@ def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None, autotune
     o.rank_cap = rank_cap
     o.oversample_q = oversample_q
     o.autotune = int(autotune)
+    o.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
     if seed is not None:
         o.seed = seed
     return o

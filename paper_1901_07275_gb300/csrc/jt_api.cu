@@ -47,6 +47,7 @@ struct jt_plan {
     // fixed one (jt_plan_set_ksplit), then the occupancy rule of the launchers.
     int ksplit_fixed[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     bool autotune = false;  // jt_batch_create measures the splits of this plan's sweeps
+    int kind = JT_FIRST_KIND;
     struct Tuned {
         int axis, fwd;
         long long nfib;
@@ -93,8 +94,14 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
             const jt::cd v = T.V[(size_t)k * N + c];
             vtab[(size_t)k * L + nu0 + c] = Cx<R>{to_r(v.real(), tag), to_r(v.imag(), tag)};
         }
+    // second kind: Im(u y) = Re((-i u) y), so the kernels take -i u_k and stay unchanged
     std::vector<Cx<R>> utab((size_t)r * n);
-    for (size_t i = 0; i < utab.size(); ++i) utab[i] = Cx<R>{to_r(T.U[i].real(), tag), to_r(T.U[i].imag(), tag)};
+    const bool second = T.kind == JT_SECOND_KIND;
+    for (size_t i = 0; i < utab.size(); ++i) {
+        const double ur = second ? T.U[i].imag() : T.U[i].real();
+        const double ui = second ? -T.U[i].real() : T.U[i].imag();
+        utab[i] = Cx<R>{to_r(ur, tag), to_r(ui, tag)};
+    }
     std::vector<R> vblk;
     if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
         // rows padded to L with zeros (warp kernel)
@@ -613,6 +620,8 @@ jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a
     jt_options_default(&o);
     if (opt) o = *opt;
     if (o.prec != JT_FP32 && o.prec != JT_SPLIT && o.prec != JT_FP64_PLAIN) return JT_EINVAL;
+    if (o.kind != JT_FIRST_KIND && o.kind != JT_SECOND_KIND) return JT_EINVAL;
+    if (o.kind == JT_SECOND_KIND && o.prec == JT_FP64_PLAIN) return JT_ENOTSUP;
     const int64_t nmax = (o.prec == JT_SPLIT) ? (int64_t(1) << jt::MAX_LOG2L_DW) : (int64_t(1) << jt::MAX_LOG2L_F32);
     for (int i = 0; i < d; ++i) {
         if (n[i] < 1 || !jt::valid_parameter(a[i]) || !jt::valid_parameter(b[i])) return JT_EINVAL;
@@ -626,6 +635,7 @@ jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a
         plan->d = d;
         plan->prec = o.prec;
         plan->autotune = o.autotune != 0;
+        plan->kind = o.kind;
         plan->axes.resize(d);
         for (int i = 0; i < d; ++i) {
             plan->n[i] = n[i];
@@ -678,7 +688,7 @@ jt_status jt_adjoint(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt
 
 jt_status jt_inverse(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt_stream_t stream) {
     if (!plan) return JT_EINVAL;
-    if (!plan->all_uniform) return JT_ENOTSUP;
+    if (!plan->all_uniform || plan->kind != JT_FIRST_KIND) return JT_ENOTSUP;
     return apply(plan, g, alpha, nrhs, false, (cudaStream_t)stream);
 }
 

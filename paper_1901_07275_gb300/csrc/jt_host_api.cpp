@@ -22,6 +22,7 @@ void jt_options_default(jt_options* opt) {
     opt->seed = 0x1901072750ULL;
     opt->fft_len_policy = 0;
     opt->autotune = 0;
+    opt->kind = JT_FIRST_KIND;
 }
 
 const char* jt_status_string(jt_status s) {

@@ -23,6 +23,7 @@ struct AxisTables {
     int nu0 = 0;        // effective split degree, min(nu0, n)
     int rank = 0;       // r
     bool uniform = true;
+    int kind = JT_FIRST_KIND;  // second kind: Vblk holds W Q~ and the transform takes Im(B o F)
     double a = 0, b = 0, eps = 0;
     double fact_err = 0;  // sampled relative Frobenius error of sum u_k v_k^T vs Z
 
@@ -32,7 +33,7 @@ struct AxisTables {
     std::vector<int32_t> m;            // FFT bin of each point
     std::vector<cd> U;                 // rank x n, row k = u_k
     std::vector<cd> V;                 // rank x N, row k = v_k
-    std::vector<double> Vblk;          // n x nu0
+    std::vector<double> Vblk;          // n x nu0: W P~_c (first kind) or W Q~_c (second kind)
     std::vector<double> sigma;         // kept singular values
 
     // orthonormal Jacobi recurrence x p_j = sg[j+1] p_{j+1} + beta[j] p_j + sg[j] p_{j-1}

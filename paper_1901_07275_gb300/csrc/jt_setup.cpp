@@ -676,7 +676,8 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
                      const jt_options& opt) {
     if (n < 1 || n > 65536 || !valid_parameter(a) || !valid_parameter(b)) return JT_EINVAL;
     if (!(eps > 0.0 && eps < 1.0)) return JT_EINVAL;
-    if (opt.nu0 < 0 || opt.nu0 > 32 || opt.oversample_q < 1 || opt.rank_cap < 0 || opt.fft_len_policy != 0 || opt.autotune < 0 || opt.autotune > 1)
+    if (opt.nu0 < 0 || opt.nu0 > 32 || opt.oversample_q < 1 || opt.rank_cap < 0 || opt.fft_len_policy != 0 || opt.autotune < 0 || opt.autotune > 1 ||
+        (opt.kind != JT_FIRST_KIND && opt.kind != JT_SECOND_KIND))
         return JT_EINVAL;
     if (points)
         for (int64_t k = 0; k < n; ++k)
@@ -735,16 +736,31 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
         int64_t mj = std::llround(t * (double)T.L / (2.0 * PI));
         T.m[j] = (int32_t)std::max<int64_t>(0, std::min<int64_t>(mj, T.L / 2));
     }
-    // dense low-degree block W V (Eq. tf:jn), by the same recurrence
+    T.kind = opt.kind;
+    // Stieltjes values for h_0 = p_0 S (the imaginary part of B, and the second-kind block)
+    if (T.N > 0 || T.kind == JT_SECOND_KIND) {
+        T.S.resize(n);
+        TanhSinh ts;
+        parallel_for(n, [&](int64_t j) {
+            double s2 = std::sin(0.5 * T.t[j]), c2 = std::cos(0.5 * T.t[j]);
+            T.S[j] = ts.stieltjes(2.0 * s2 * s2, 2.0 * c2 * c2, a, b);
+        });
+    }
+    // dense low-degree block W V (Eq. tf:jn), by the same recurrence: rowP p_c (first kind)
+    // or rowQ h_c, with h_1 = ((x - beta_0) h_0 - mu0^{1/2}) / sg_1 (second kind)
     T.Vblk.assign((size_t)n * T.nu0, 0.0);
     if (T.nu0 > 0)
         parallel_for(n, [&](int64_t j) {
             DD x;
             make_x(T.t[j], x);
-            DD pm = dd(0), pc = dd(C.p0);
+            const bool second = T.kind == JT_SECOND_KIND;
+            DD pm = dd(0), pc = second ? dd(C.p0) * T.S[j] : dd(C.p0);
+            const double row = second ? T.rowQ[j] : T.rowP[j];
             for (int c = 0; c < T.nu0; ++c) {
-                T.Vblk[(size_t)j * T.nu0 + c] = T.rowP[j] * todouble(pc);
-                DD pn = ((x - C.betaD[c]) * pc - C.sgD[c] * pm) * C.isgD[c + 1];
+                T.Vblk[(size_t)j * T.nu0 + c] = row * todouble(pc);
+                DD pn = (x - C.betaD[c]) * pc - C.sgD[c] * pm;
+                if (second && c == 0) pn = pn - dd(C.sqrt_mu0);
+                pn = pn * C.isgD[c + 1];
                 pm = pc;
                 pc = pn;
             }
@@ -753,12 +769,6 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
         T.rank = 0;
         return JT_OK;
     }
-    T.S.resize(n);
-    TanhSinh ts;
-    parallel_for(n, [&](int64_t j) {
-        double s2 = std::sin(0.5 * T.t[j]), c2 = std::cos(0.5 * T.t[j]);
-        T.S[j] = ts.stieltjes(2.0 * s2 * s2, 2.0 * c2 * c2, a, b);
-    });
 
     Entries E(T, C);
     int cap = opt.rank_cap;

@@ -19,10 +19,11 @@ class Transform:
     Inputs are torch tensors on the plan's CUDA device, contiguous, of shape
     ``(..., n_0, .., n_{d-1})`` -- leading dimensions are independent right-hand sides --
     and dtype float32 (``precision="fp32"``) or float64 (``"split"``, ``"fp64_plain"``).
+    ``kind="second"`` expands in the second-kind functions Q~ (forward and adjoint only).
     """
 
     def __init__(self, n, a, b, points=None, eps=None, precision="fp32", nu0=27, rank_cap=0,
-                 oversample_q=3, seed=None, autotune=False, stream=None):
+                 oversample_q=3, seed=None, autotune=False, kind="first", stream=None):
         import torch
 
         self.n = tuple(int(v) for v in n)
@@ -33,8 +34,9 @@ class Transform:
         self.eps = _DEFAULT_EPS[precision] if eps is None else float(eps)
         self.dtype = getattr(torch, _DTYPES[precision])
         self.uniform = points is None or all(p is None for p in points)
+        self.kind = kind
         opt = B.options(precision, nu0=nu0, rank_cap=rank_cap, oversample_q=oversample_q, seed=seed,
-                        autotune=1 if autotune else 0)
+                        autotune=1 if autotune else 0, kind=kind)
         s = self._stream(stream)
         self._plan = B.jt_plan_create(self.n, self.a, self.b, points, self.eps, opt, s)
         self.info = [B.jt_plan_info(self._plan, i, self.n[i]) for i in range(self.d)]

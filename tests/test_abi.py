@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_defaults_and_status_strings(lib):
     o = B.Options()
     lib.jt_options_default(ctypes.byref(o))
-    assert (o.prec, o.nu0, o.rank_cap, o.oversample_q, o.fft_len_policy, o.autotune) == (0, 27, 0, 3, 0, 0)
+    assert (o.prec, o.nu0, o.rank_cap, o.oversample_q, o.fft_len_policy, o.autotune, o.kind) == (0, 27, 0, 3, 0, 0, 0)
     for s in range(7):
         assert B.status_string(s).startswith("JT_")
 

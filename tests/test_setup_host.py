@@ -134,3 +134,46 @@ def test_factorisation_is_deterministic_and_seeded():
     assert np.array_equal(T1.U, T1b.U) and np.array_equal(T1.V, T1b.V)
     D1, D2 = dense_from_tables(T1), dense_from_tables(T2)
     assert np.linalg.norm(D1 - D2) / np.linalg.norm(D1) < 1e-9
+
+
+# ------------------------------------------------------------------ second kind
+def dense_from_tables_second_kind(T: B.AxisTables) -> np.ndarray:
+    """[W Vq, Im((sum_k u_k v_k^T) o F)]: the second-kind matrix the kernels apply."""
+    n, nu0 = T.n, T.nu0
+    G = T.U.T @ T.V
+    F = np.exp(2j * np.pi * np.outer(T.m, np.arange(nu0, n)) / T.L)
+    return np.concatenate([T.vblk, np.imag(G * F)], axis=1)
+
+
+@pytest.mark.parametrize(
+    "a,b,n,eps",
+    [(-0.25, 0.5, 512, 1e-12), (0.3, -0.4, 200, 1e-12), (0.0, 0.0, 64, 1e-12), (0.8, -0.7, 300, 1e-12),
+     (-0.5, -0.5, 40, 1e-12), (0.25, 0.25, 27, 1e-12), (0.1, 0.2, 5, 1e-12)],
+)
+def test_second_kind_tables_rebuild_the_weighted_matrix(a, b, n, eps):
+    """Second-kind plans (reading: Q~ = M sin psi): the dense block holds sqrt(w_k) Q~_c(t_k)
+    and Im(B o F) the higher degrees, against the oracle's quadrature-based Q~."""
+    opt = B.options("split", kind="second")
+    T = B.AxisTables(n, a, b, eps=eps, opt=opt)
+    Mq = oracle.uniform_matrix_q(a, b, n)
+    D = dense_from_tables_second_kind(T)
+    assert np.linalg.norm(D - Mq) <= 1e-10 * np.linalg.norm(Mq)
+
+
+@pytest.mark.parametrize("a,b", [(0.25, 0.25), (-0.6, 0.3)])
+def test_second_kind_tables_nonuniform(a, b):
+    n = 150
+    t = np.sort(np.pi * np.random.default_rng(7).uniform(size=n))
+    opt = B.options("split", kind="second")
+    T = B.AxisTables(n, a, b, points=t, eps=1e-12, opt=opt)
+    Mq = oracle.nonuniform_matrix_q(t, a, b, n)
+    D = dense_from_tables_second_kind(T)
+    assert np.linalg.norm(D - Mq) <= 1e-10 * np.linalg.norm(Mq)
+
+
+def test_kind_option_is_validated():
+    opt = B.options("fp32")
+    opt.kind = 2
+    with pytest.raises(B.JTError) as e:
+        B.AxisTables(64, 0.1, 0.2, opt=opt)
+    assert e.value.status == B.JT_EINVAL
