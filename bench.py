@@ -547,6 +547,29 @@ def main():
                               "speedup_split_over_plain": split_v / plain_v}
         Tp.close()
 
+        # second-kind transform (Q~) on the same workload: forward + adjoint, FP32
+        Tq = Transform(N, [p[0] for p in AB], [p[1] for p in AB], eps=1e-7, kind="second")
+        for _ in range(2):
+            Tq.forward(x, out=f)
+            Tq.adjoint(f, out=y)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        kq = 5
+        for _ in range(kq):
+            Tq.forward(x, out=f)
+            Tq.adjoint(f, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        q_ms = e0.elapsed_time(e1) / kq
+        mq = [oracle.uniform_matrix_q(a, b, m) for (a, b), m in zip(AB, N)]
+        refq = oracle.forward(alpha[:1], mq)
+        Tq.forward(x, out=f)
+        errq = float(np.linalg.norm(f[:1].double().cpu().numpy() - refq) / np.linalg.norm(refq))
+        line["second_kind"] = {"value": coeffs_per_step / (q_ms * 1e-3), "unit": UNIT, "nrhs": nrhs,
+                               "ms_per_step": q_ms, "step": "forward + adjoint", "ranks": Tq.ranks,
+                               "rel_err_forward": errq}
+        Tq.close()
+
         line["other_configs"] = other_configs(dev, stream)
         line["batch"] = batch_mix_throughput(dev, stream)
 
