@@ -316,6 +316,18 @@ def batch_mix_throughput(dev, stream, count=64):
     mix = syn.batch_mix(count)
     Ts = [Transform(m["n"], [p[0] for p in m["ab"]], [p[1] for p in m["ab"]], eps=1e-7) for m in mix]
     setup_s = time.perf_counter() - t0
+    # the same plans with their host setups side by side, and reloaded from saved bytes
+    t0 = time.perf_counter()
+    many = Transform.create_many([{"n": m["n"], "a": [p[0] for p in m["ab"]], "b": [p[1] for p in m["ab"]],
+                                   "eps": 1e-7} for m in mix])
+    many_s = time.perf_counter() - t0
+    saved = [T.save() for T in Ts]
+    t0 = time.perf_counter()
+    loaded = [Transform.load(b) for b in saved]
+    load_s = time.perf_counter() - t0
+    same = all(a.save() == b for a, b in zip(many, saved))
+    for T in many + loaded:
+        T.close()
     xs = [torch.tensor(syn.normal(2000 + i, 0, (m["nrhs"],) + tuple(m["n"])), dtype=torch.float32, device=dev)
           for i, m in enumerate(mix)]
     fs = [torch.empty_like(x) for x in xs]
@@ -354,6 +366,8 @@ def batch_mix_throughput(dev, stream, count=64):
         batch.adjoint(fs, gs, stream=side)
     ms_graph = timed(graph.replay)
     out = {"members": count, "coeffs_per_step": coeffs, "plan_setup_s": setup_s,
+           "plan_setup_many_s": many_s, "plan_load_s": load_s, "saved_bytes": sum(len(b) for b in saved),
+           "many_equals_one_by_one": same,
            "batched": {"coeffs_per_s": coeffs / (ms_batch * 1e-3), "ms_per_step": ms_batch},
            "graph_replay": {"coeffs_per_s": coeffs / (ms_graph * 1e-3), "ms_per_step": ms_graph},
            "one_by_one": {"coeffs_per_s": coeffs / (ms_single * 1e-3), "ms_per_step": ms_single}}

@@ -37,6 +37,7 @@
 #ifndef JT_H
 #define JT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -150,8 +151,48 @@ jt_status jt_forward_plain_noalloc(jt_plan* plan, const void* alpha, void* f, in
 jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_len, double* t_out,
                        double* w_out);
 
+/* Dimensions and options of a plan (any output pointer may be NULL): the number of axes,
+ * n[0..d-1] (n[d..2] set to 1), the precision, the kind, and whether every axis uses the
+ * Gauss--Jacobi nodes (so that jt_inverse is defined for the first kind). */
+jt_status jt_plan_shape(const jt_plan* plan, int* d, int64_t* n, int* prec, int* kind, int* all_uniform);
+
 /* Release a plan and its device tables.  NULL is accepted. */
 void jt_destroy(jt_plan* plan);
+
+/* ------------------------------------------------------------------------------------
+ * Serving helpers (no counterpart in the paper, whose setup runs once per experiment):
+ * setting up many plans at once, and saving / loading the result of a plan's setup.
+ * ------------------------------------------------------------------------------------ */
+
+/* The arguments of one jt_plan_create call. */
+typedef struct {
+    int32_t d;
+    int64_t n[3];
+    double a[3], b[3];
+    const double* points[3]; /* per axis as in jt_plan_create (all NULL: Gauss--Jacobi nodes) */
+    double eps;
+    const jt_options* opt;   /* NULL for defaults */
+} jt_plan_desc;
+
+/* Create `count` plans: the host setups run side by side on the host cores, then the tables
+ * are uploaded on `stream` (synchronised).  On success out[i] is the plan of descs[i]; on any
+ * error every out[i] is NULL, nothing is leaked and the first failing status is returned. */
+jt_status jt_plan_create_many(int count, jt_plan** out, const jt_plan_desc* descs, jt_stream_t stream);
+
+/* Serialise the setup of a plan (nodes, weights, bins, factors, dense block: every table
+ * jt_plan_create computed, in FP64) into buf, a byte array that jt_plan_load accepts on any
+ * little-endian host.  Schedules (jt_plan_set_ksplit / jt_plan_tune) are not saved: they
+ * belong to the GPU that measured them.  With buf NULL, *size receives the bytes needed and
+ * the call returns JT_OK; with *size too small, *size receives the bytes needed and the call
+ * returns JT_EINVAL; otherwise the plan is written and *size set to its length.  The plan is
+ * only read. */
+jt_status jt_plan_save(const jt_plan* plan, void* buf, size_t* size);
+
+/* Recreate a plan from jt_plan_save bytes without any setup work: the buffer is checked
+ * (magic, version, checksum, every size and range; JT_EINVAL before any GPU call if it does
+ * not pass), then the tables are uploaded on `stream` (synchronised).  The loaded plan
+ * computes bit for bit what the saved one did. */
+jt_status jt_plan_load(jt_plan** out, const void* buf, size_t size, jt_stream_t stream);
 
 /* ------------------------------------------------------------------------------------
  * Schedules (no counterpart in the paper, which applies the rank terms one after another

@@ -31,6 +31,10 @@ EXPORTS = (
     "jt_forward_plain_noalloc",
     "jt_plan_info",
     "jt_destroy",
+    "jt_plan_shape",
+    "jt_plan_create_many",
+    "jt_plan_save",
+    "jt_plan_load",
     "jt_plan_set_ksplit",
     "jt_plan_tune",
     "jt_plan_schedule",
@@ -51,6 +55,18 @@ class JTError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
         super().__init__(f"{what}: {status_string(status)}")
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int32),
+        ("n", ctypes.c_int64 * 3),
+        ("a", ctypes.c_double * 3),
+        ("b", ctypes.c_double * 3),
+        ("points", ctypes.POINTER(ctypes.c_double) * 3),
+        ("eps", ctypes.c_double),
+        ("opt", ctypes.c_void_p),
+    ]
 
 
 class Options(ctypes.Structure):
@@ -92,6 +108,15 @@ def lib() -> ctypes.CDLL:
     L.jt_plan_info.restype = i32
     L.jt_destroy.argtypes = [vp]
     L.jt_destroy.restype = None
+    L.jt_plan_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.jt_plan_shape.restype = i32
+    L.jt_plan_create_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(PlanDesc), vp]
+    L.jt_plan_create_many.restype = i32
+    L.jt_plan_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.jt_plan_save.restype = i32
+    L.jt_plan_load.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_size_t, vp]
+    L.jt_plan_load.restype = i32
     L.jt_plan_set_ksplit.argtypes = [vp, i32, i32, i32]
     L.jt_plan_set_ksplit.restype = i32
     L.jt_plan_tune.argtypes = [vp, i64, vp]
@@ -209,6 +234,64 @@ def jt_plan_info(plan: int, axis: int, n: int | None = None):
 
 def jt_destroy(plan: int) -> None:
     lib().jt_destroy(_ptr(plan))
+
+
+def jt_plan_shape(plan: int):
+    """``{"d", "n", "prec", "kind", "all_uniform"}`` of a plan."""
+    d, prec, kind, uni = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    n = (ctypes.c_int64 * 3)()
+    _check(lib().jt_plan_shape(_ptr(plan), ctypes.byref(d), n, ctypes.byref(prec), ctypes.byref(kind),
+                               ctypes.byref(uni)), "jt_plan_shape")
+    return {"d": d.value, "n": tuple(n[: d.value]), "prec": prec.value, "kind": kind.value,
+            "all_uniform": bool(uni.value)}
+
+
+def jt_plan_create_many(specs, stream: int = 0):
+    """Create several plans at once; ``specs`` holds dicts with ``n, a, b`` and optionally
+    ``points, eps, opt`` (as for :func:`jt_plan_create`).  Returns the handles."""
+    count = len(specs)
+    descs = (PlanDesc * max(count, 1))()
+    keep = []
+    for i, sp in enumerate(specs):
+        D = descs[i]
+        d = len(sp["n"])
+        D.d = d
+        for k in range(d):
+            D.n[k] = int(sp["n"][k])
+            D.a[k] = float(sp["a"][k])
+            D.b[k] = float(sp["b"][k])
+        pts = sp.get("points")
+        if pts is not None:
+            for k, p in enumerate(pts):
+                if p is not None:
+                    arr = np.ascontiguousarray(p, dtype=np.float64)
+                    keep.append(arr)
+                    D.points[k] = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        D.eps = float(sp.get("eps", 1e-7))
+        opt = sp.get("opt")
+        if opt is not None:
+            keep.append(opt)
+            D.opt = ctypes.cast(ctypes.byref(opt), ctypes.c_void_p)
+    out = (ctypes.c_void_p * max(count, 1))()
+    _check(lib().jt_plan_create_many(count, out, descs, _ptr(stream)), "jt_plan_create_many")
+    return [out[i] for i in range(count)]
+
+
+def jt_plan_save(plan: int) -> bytes:
+    """The serialised setup of a plan (see jt_plan_save in jt.h)."""
+    size = ctypes.c_size_t(0)
+    _check(lib().jt_plan_save(_ptr(plan), None, ctypes.byref(size)), "jt_plan_save")
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib().jt_plan_save(_ptr(plan), buf, ctypes.byref(size)), "jt_plan_save")
+    return buf.raw[: size.value]
+
+
+def jt_plan_load(data: bytes, stream: int = 0) -> int:
+    """Recreate a plan from :func:`jt_plan_save` bytes; returns the handle."""
+    h = ctypes.c_void_p()
+    raw = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(lib().jt_plan_load(ctypes.byref(h), raw, len(data), _ptr(stream)), "jt_plan_load")
+    return h.value
 
 
 def jt_plan_set_ksplit(plan: int, axis: int, direction: int, ksplit: int) -> None:

@@ -9,9 +9,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -611,14 +613,13 @@ void jt_batch_destroy(jt_batch* batch) {
     delete batch;
 }
 
-jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a, const double* b,
-                         const double* const* points, double eps, const jt_options* opt, jt_stream_t stream) {
-    if (!out) return JT_EINVAL;
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Argument checks of jt_plan_create (JT_OK or the status to return).
+jt_status check_plan_args(int d, const int64_t* n, const double* a, const double* b, double eps, const jt_options& o) {
     if (d < 1 || d > 3 || !n || !a || !b) return JT_EINVAL;
-    jt_options o;
-    jt_options_default(&o);
-    if (opt) o = *opt;
     if (o.prec != JT_FP32 && o.prec != JT_SPLIT && o.prec != JT_FP64_PLAIN) return JT_EINVAL;
     if (o.kind != JT_FIRST_KIND && o.kind != JT_SECOND_KIND) return JT_EINVAL;
     if (o.kind == JT_SECOND_KIND && o.prec == JT_FP64_PLAIN) return JT_ENOTSUP;
@@ -628,51 +629,254 @@ jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a
         if (n[i] > nmax) return JT_ENOTSUP;
     }
     if (!(eps > 0.0 && eps < 1.0)) return JT_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
+    return JT_OK;
+}
+
+int log2_of(int64_t L) {
+    int lg = 0;
+    while ((int64_t(1) << lg) < L) ++lg;
+    return lg;
+}
+
+// Host phase of plan creation: the setup of every axis (no GPU).
+jt_status plan_host_setup(jt_plan* plan, int d, const int64_t* n, const double* a, const double* b,
+                          const double* const* points, double eps, const jt_options& o) {
+    plan->d = d;
+    plan->prec = o.prec;
+    plan->autotune = o.autotune != 0;
+    plan->kind = o.kind;
+    plan->axes.resize(d);
+    for (int i = 0; i < d; ++i) {
+        plan->n[i] = n[i];
+        const double* pts = points ? points[i] : nullptr;
+        if (pts) plan->all_uniform = false;
+        jt_status st = jt::axis_setup(plan->axes[i].host, n[i], a[i], b[i], pts, eps, o);
+        if (st != JT_OK) return st;
+        plan->axes[i].log2L = log2_of(plan->axes[i].host.L);
+    }
+    return JT_OK;
+}
+
+// Device phase: upload the working-precision tables (or build the plain FP64 resources).
+jt_status plan_device_setup(jt_plan* plan, cudaStream_t s) {
+    for (auto& ax : plan->axes) {
+        jt_status st = JT_OK;
+        if (plan->prec == JT_FP32)
+            st = build_device_axis<float>(ax, s);
+        else if (plan->prec == JT_SPLIT)
+            st = build_device_axis<dw>(ax, s);
+        if (st != JT_OK) return st;
+    }
+    if (plan->prec == JT_FP64_PLAIN) {
+        std::vector<const jt::AxisTables*> tabs;
+        for (auto& ax : plan->axes) tabs.push_back(&ax.host);
+        return jt::plain_create(&plan->plain, tabs, s);
+    }
+    return JT_OK;
+}
+
+// Serialised plan: magic, version, plan fields, the tables of each axis, FNV-1a checksum.
+const unsigned char PLAN_MAGIC[8] = {'J', 'T', 'P', 'L', 'A', 'N', 0, 1};
+constexpr uint32_t PLAN_VERSION = 1;
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+template <class T>
+void put_raw(std::vector<unsigned char>& out, const T& v) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    out.insert(out.end(), p, p + sizeof(T));
+}
+template <class T>
+bool get_raw(const unsigned char*& p, const unsigned char* end, T& v) {
+    if ((size_t)(end - p) < sizeof(T)) return false;
+    std::memcpy(&v, p, sizeof(T));
+    p += sizeof(T);
+    return true;
+}
+
+void serialize_plan(const jt_plan* plan, std::vector<unsigned char>& out) {
+    out.insert(out.end(), PLAN_MAGIC, PLAN_MAGIC + 8);
+    put_raw<uint32_t>(out, PLAN_VERSION);
+    put_raw<int32_t>(out, plan->d);
+    put_raw<int32_t>(out, plan->prec);
+    put_raw<int32_t>(out, plan->kind);
+    put_raw<int32_t>(out, plan->autotune ? 1 : 0);
+    put_raw<int32_t>(out, plan->all_uniform ? 1 : 0);
+    for (int i = 0; i < 3; ++i) put_raw<int64_t>(out, plan->n[i]);
+    for (int i = 0; i < plan->d; ++i) jt::serialize_tables(plan->axes[i].host, out);
+    put_raw<uint64_t>(out, fnv1a(out.data(), out.size()));
+}
+
+// Parse and check a serialised plan into the host fields of *plan (no GPU).
+jt_status deserialize_plan(const unsigned char* buf, size_t size, jt_plan* plan) {
+    if (!buf || size < 8 + 4 + 8) return JT_EINVAL;
+    if (std::memcmp(buf, PLAN_MAGIC, 8) != 0) return JT_EINVAL;
+    uint64_t sum = 0;
+    std::memcpy(&sum, buf + size - 8, 8);
+    if (sum != fnv1a(buf, size - 8)) return JT_EINVAL;
+    const unsigned char* p = buf + 8;
+    const unsigned char* end = buf + size - 8;
+    uint32_t version = 0;
+    int32_t d = 0, prec = 0, kind = 0, autotune = 0, uni = 0;
+    if (!get_raw(p, end, version) || version != PLAN_VERSION || !get_raw(p, end, d) || !get_raw(p, end, prec) ||
+        !get_raw(p, end, kind) || !get_raw(p, end, autotune) || !get_raw(p, end, uni))
+        return JT_EINVAL;
+    if (d < 1 || d > 3 || (prec != JT_FP32 && prec != JT_SPLIT && prec != JT_FP64_PLAIN)) return JT_EINVAL;
+    if ((kind != JT_FIRST_KIND && kind != JT_SECOND_KIND) || (kind == JT_SECOND_KIND && prec == JT_FP64_PLAIN))
+        return JT_EINVAL;
+    plan->d = d;
+    plan->prec = prec;
+    plan->kind = kind;
+    plan->autotune = autotune != 0;
+    plan->all_uniform = uni != 0;
+    for (int i = 0; i < 3; ++i)
+        if (!get_raw(p, end, plan->n[i])) return JT_EINVAL;
+    const int64_t nmax = (prec == JT_SPLIT) ? (int64_t(1) << jt::MAX_LOG2L_DW) : (int64_t(1) << jt::MAX_LOG2L_F32);
+    plan->axes.resize(d);
+    bool all_uni = true;
+    for (int i = 0; i < d; ++i) {
+        jt::AxisTables& T = plan->axes[i].host;
+        if (!jt::deserialize_tables(p, end, T, nmax)) return JT_EINVAL;
+        if (T.n != plan->n[i] || T.kind != kind) return JT_EINVAL;
+        all_uni = all_uni && T.uniform;
+        plan->axes[i].log2L = log2_of(T.L);
+    }
+    if (p != end || all_uni != plan->all_uniform) return JT_EINVAL;
+    return JT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jt_status jt_plan_create(jt_plan** out, int d, const int64_t* n, const double* a, const double* b,
+                         const double* const* points, double eps, const jt_options* opt, jt_stream_t stream) {
+    if (!out) return JT_EINVAL;
+    *out = nullptr;
+    jt_options o;
+    jt_options_default(&o);
+    if (opt) o = *opt;
+    jt_status st = check_plan_args(d, n, a, b, eps, o);
+    if (st != JT_OK) return st;
     jt_plan* plan = nullptr;
     try {
         plan = new jt_plan();
-        plan->d = d;
-        plan->prec = o.prec;
-        plan->autotune = o.autotune != 0;
-        plan->kind = o.kind;
-        plan->axes.resize(d);
-        for (int i = 0; i < d; ++i) {
-            plan->n[i] = n[i];
-            const double* pts = points ? points[i] : nullptr;
-            if (pts) plan->all_uniform = false;
-            jt_status st = jt::axis_setup(plan->axes[i].host, n[i], a[i], b[i], pts, eps, o);
-            if (st != JT_OK) {
-                jt_destroy(plan);
-                return st;
-            }
-            int lg = 0;
-            while ((int64_t(1) << lg) < plan->axes[i].host.L) ++lg;
-            plan->axes[i].log2L = lg;
-            if (o.prec == JT_FP32)
-                st = build_device_axis<float>(plan->axes[i], s);
-            else if (o.prec == JT_SPLIT)
-                st = build_device_axis<dw>(plan->axes[i], s);
-            if (st != JT_OK) {
-                jt_destroy(plan);
-                return st;
-            }
-        }
-        if (o.prec == JT_FP64_PLAIN) {
-            std::vector<const jt::AxisTables*> tabs;
-            for (auto& ax : plan->axes) tabs.push_back(&ax.host);
-            jt_status st = jt::plain_create(&plan->plain, tabs, s);
-            if (st != JT_OK) {
-                jt_destroy(plan);
-                return st;
-            }
-        }
+        st = plan_host_setup(plan, d, n, a, b, points, eps, o);
+        if (st == JT_OK) st = plan_device_setup(plan, (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {
+        st = JT_ENOMEM;
+    } catch (...) {
+        st = JT_EINVAL;
+    }
+    if (st != JT_OK) {
         jt_destroy(plan);
+        return st;
+    }
+    *out = plan;
+    return JT_OK;
+}
+
+jt_status jt_plan_create_many(int count, jt_plan** out, const jt_plan_desc* descs, jt_stream_t stream) {
+    if (count < 0 || (count > 0 && (!out || !descs))) return JT_EINVAL;
+    for (int i = 0; i < count; ++i) out[i] = nullptr;
+    std::vector<jt_options> opts(count);
+    for (int i = 0; i < count; ++i) {
+        jt_options_default(&opts[i]);
+        if (descs[i].opt) opts[i] = *descs[i].opt;
+        const jt_status st = check_plan_args(descs[i].d, descs[i].n, descs[i].a, descs[i].b, descs[i].eps, opts[i]);
+        if (st != JT_OK) return st;
+    }
+    std::vector<jt_plan*> plans(count, nullptr);
+    std::vector<jt_status> status(count, JT_OK);
+    try {
+        for (int i = 0; i < count; ++i) plans[i] = new jt_plan();
+        // host setups side by side: W workers, each plan's own setup with hw / W threads
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int workers = (int)std::min<unsigned>((unsigned)std::max(count, 1), std::min(hw, 16u));
+        const int inner = std::max(1, (int)std::min(hw, 16u) / std::max(workers, 1));
+        std::atomic_int next(0);
+        auto work = [&]() {
+            jt::set_setup_threads(inner);
+            for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+                try {
+                    const jt_plan_desc& D = descs[i];
+                    const double* const* pts = D.points[0] || D.points[1] || D.points[2] ? D.points : nullptr;
+                    status[i] = plan_host_setup(plans[i], D.d, D.n, D.a, D.b, pts, D.eps, opts[i]);
+                } catch (const std::bad_alloc&) {
+                    status[i] = JT_ENOMEM;
+                } catch (...) {
+                    status[i] = JT_EINVAL;
+                }
+            }
+        };
+        std::vector<std::thread> th;
+        for (int w = 1; w < workers; ++w) th.emplace_back(work);
+        work();
+        for (auto& t : th) t.join();
+        for (int i = 0; i < count; ++i)
+            if (status[i] == JT_OK) status[i] = plan_device_setup(plans[i], (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        for (auto* p : plans) jt_destroy(p);
         return JT_ENOMEM;
     } catch (...) {
-        jt_destroy(plan);
+        for (auto* p : plans) jt_destroy(p);
         return JT_EINVAL;
+    }
+    for (int i = 0; i < count; ++i)
+        if (status[i] != JT_OK) {
+            const jt_status st = status[i];
+            for (auto* p : plans) jt_destroy(p);
+            return st;
+        }
+    for (int i = 0; i < count; ++i) out[i] = plans[i];
+    return JT_OK;
+}
+
+jt_status jt_plan_save(const jt_plan* plan, void* buf, size_t* size) {
+    if (!plan || !size) return JT_EINVAL;
+    try {
+        std::vector<unsigned char> bytes;
+        serialize_plan(plan, bytes);
+        if (!buf) {
+            *size = bytes.size();
+            return JT_OK;
+        }
+        if (*size < bytes.size()) {
+            *size = bytes.size();
+            return JT_EINVAL;
+        }
+        std::memcpy(buf, bytes.data(), bytes.size());
+        *size = bytes.size();
+        return JT_OK;
+    } catch (...) {
+        return JT_ENOMEM;
+    }
+}
+
+jt_status jt_plan_load(jt_plan** out, const void* buf, size_t size, jt_stream_t stream) {
+    if (!out) return JT_EINVAL;
+    *out = nullptr;
+    jt_plan* plan = nullptr;
+    jt_status st;
+    try {
+        plan = new jt_plan();
+        st = deserialize_plan(static_cast<const unsigned char*>(buf), size, plan);
+        if (st == JT_OK) st = plan_device_setup(plan, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        st = JT_ENOMEM;
+    } catch (...) {
+        st = JT_EINVAL;
+    }
+    if (st != JT_OK) {
+        jt_destroy(plan);
+        return st;
     }
     *out = plan;
     return JT_OK;
@@ -744,6 +948,17 @@ jt_status jt_plan_schedule(const jt_plan* plan, int axis, int direction, int64_t
     long long inner = 1;
     for (int i = axis + 1; i < plan->d; ++i) inner *= plan->n[i];
     *ksplit = sweep_ksplit(plan, axis, direction == 0, total / plan->n[axis], inner > 1);
+    return JT_OK;
+}
+
+jt_status jt_plan_shape(const jt_plan* plan, int* d, int64_t* n, int* prec, int* kind, int* all_uniform) {
+    if (!plan) return JT_EINVAL;
+    if (d) *d = plan->d;
+    if (n)
+        for (int i = 0; i < 3; ++i) n[i] = (i < plan->d) ? plan->n[i] : 1;
+    if (prec) *prec = plan->prec;
+    if (kind) *kind = plan->kind;
+    if (all_uniform) *all_uniform = plan->all_uniform ? 1 : 0;
     return JT_OK;
 }
 

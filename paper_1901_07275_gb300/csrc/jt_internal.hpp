@@ -52,4 +52,13 @@ void axis_b_rows(const AxisTables& T, const int64_t* rows, int64_t nrows, cd* ou
 // Validation shared by the C entry points.
 bool valid_parameter(double v);
 
+// Plan serialisation (jt_serialize.cpp): append the tables of one axis to out; read them
+// back, checking every size and range (false on a malformed or truncated buffer).
+void serialize_tables(const AxisTables& T, std::vector<unsigned char>& out);
+bool deserialize_tables(const unsigned char*& p, const unsigned char* end, AxisTables& T, int64_t nmax);
+
+// Upper bound on the setup threads of the calling thread (jt_plan_create_many lowers it in
+// its workers so that plans set up side by side do not oversubscribe the host).
+void set_setup_threads(int n);
+
 }  // namespace jt

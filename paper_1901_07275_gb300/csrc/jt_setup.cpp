@@ -168,11 +168,13 @@ inline void make_x(double t, DD& x) {
     }
 }
 
+thread_local int g_setup_threads = 16;
+
 template <class F>
 void parallel_for(int64_t count, F&& fn) {
     if (count <= 0) return;
     unsigned hw = std::thread::hardware_concurrency();
-    int64_t nt = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), (int64_t)16, count}));
+    int64_t nt = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), (int64_t)g_setup_threads, count}));
     if (nt == 1) {
         for (int64_t i = 0; i < count; ++i) fn(i);
         return;
@@ -811,5 +813,7 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
         r = std::min(cap, 2 * r);
     }
 }
+
+void set_setup_threads(int n) { g_setup_threads = n < 1 ? 1 : (n > 16 ? 16 : n); }
 
 }  // namespace jt

@@ -41,6 +41,48 @@ class Transform:
         self._plan = B.jt_plan_create(self.n, self.a, self.b, points, self.eps, opt, s)
         self.info = [B.jt_plan_info(self._plan, i, self.n[i]) for i in range(self.d)]
 
+    @classmethod
+    def _from_handle(cls, plan):
+        """Wrap an existing plan handle (from jt_plan_load or jt_plan_create_many)."""
+        import torch
+
+        self = cls.__new__(cls)
+        sh = B.jt_plan_shape(plan)
+        self._plan = plan
+        self.n = sh["n"]
+        self.d = sh["d"]
+        self.precision = {B.JT_FP32: "fp32", B.JT_SPLIT: "split", B.JT_FP64_PLAIN: "fp64_plain"}[sh["prec"]]
+        self.kind = "second" if sh["kind"] == B.JT_SECOND_KIND else "first"
+        self.dtype = getattr(torch, _DTYPES[self.precision])
+        self.uniform = sh["all_uniform"]
+        self.a = self.b = None
+        self.eps = None
+        self.info = [B.jt_plan_info(plan, i, self.n[i]) for i in range(self.d)]
+        return self
+
+    def save(self) -> bytes:
+        """The plan's setup as bytes (:meth:`load` recreates it without setup work)."""
+        return B.jt_plan_save(self._plan)
+
+    @classmethod
+    def load(cls, data: bytes, stream=None):
+        """A plan from :meth:`save` bytes: only the device upload runs."""
+        return cls._from_handle(B.jt_plan_load(data, cls._stream(stream)))
+
+    @classmethod
+    def create_many(cls, specs, stream=None):
+        """Several plans whose host setups run side by side.  ``specs``: dicts with ``n, a, b``
+        and optionally ``points, eps, precision, kind, nu0, rank_cap, oversample_q, seed``."""
+        raw = []
+        for sp in specs:
+            prec = sp.get("precision", "fp32")
+            opt = B.options(prec, nu0=sp.get("nu0", 27), rank_cap=sp.get("rank_cap", 0),
+                            oversample_q=sp.get("oversample_q", 3), seed=sp.get("seed"),
+                            kind=sp.get("kind", "first"))
+            raw.append({"n": sp["n"], "a": sp["a"], "b": sp["b"], "points": sp.get("points"),
+                        "eps": sp.get("eps", _DEFAULT_EPS[prec]), "opt": opt})
+        return [cls._from_handle(h) for h in B.jt_plan_create_many(raw, cls._stream(stream))]
+
     @staticmethod
     def _stream(stream):
         import torch

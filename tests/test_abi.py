@@ -87,3 +87,29 @@ def test_axis_tables_reject_bad_arguments(lib):
     for args in [(0, 0.0, 0.0), (10, -1.0, 0.0), (10, 0.0, 1.0)]:
         with pytest.raises(B.JTError):
             B.AxisTables(*args)
+
+
+def test_plan_load_rejects_malformed_bytes_before_any_gpu_call(lib):
+    """jt_plan_load checks magic, version, checksum and every size on the host; none of these
+    buffers reaches the device upload (this test runs without a GPU)."""
+    bad = [b"", b"JTPLAN", b"\x00" * 64, b"JTPLAN\x00\x01" + b"\x00" * 40,
+           b"JTPLAN\x00\x01" + bytes(range(200))]
+    for data in bad:
+        with pytest.raises(B.JTError) as e:
+            B.jt_plan_load(data)
+        assert e.value.status == B.JT_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.jt_plan_load(ctypes.byref(h), None, 100, None) == B.JT_EINVAL
+    assert lib.jt_plan_load(None, b"x", 1, None) == B.JT_EINVAL
+
+
+def test_plan_save_and_create_many_argument_checks(lib):
+    size = ctypes.c_size_t(0)
+    assert lib.jt_plan_save(None, None, ctypes.byref(size)) == B.JT_EINVAL
+    assert lib.jt_plan_create_many(0, None, None, None) == B.JT_OK
+    assert lib.jt_plan_create_many(-1, None, None, None) == B.JT_EINVAL
+    # a descriptor with a parameter outside (-1, 1) is rejected before any setup or upload
+    with pytest.raises(B.JTError) as e:
+        B.jt_plan_create_many([{"n": [64], "a": [0.1], "b": [0.2]}, {"n": [64], "a": [1.5], "b": [0.2]}])
+    assert e.value.status == B.JT_EINVAL
+    assert lib.jt_plan_shape(None, None, None, None, None, None) == B.JT_EINVAL
