@@ -303,6 +303,26 @@ def other_configs(dev, stream):
     return out
 
 
+def setup_timings():
+    """Plan creation time (host FP64/double-word setup, then the upload) for the longest axes,
+    with the O(n^2) steps on the host cores or in FP64 kernels on the GPU (setup_device)."""
+    from paper_1901_07275_gb300 import Transform
+
+    out = {}
+    for label, n, prec, eps in (("1d-16384 fp32 eps 1e-7", 16384, "fp32", 1e-7),
+                                ("1d-8192 split eps 1e-12", 8192, "split", 1e-12),
+                                ("1d-4096 fp32 eps 1e-7", 4096, "fp32", 1e-7)):
+        row = {}
+        for dev_setup in (False, True):
+            t0 = time.perf_counter()
+            T = Transform((n,), [0.1], [-0.3], eps=eps, precision=prec, setup_device=dev_setup)
+            row["gpu_setup_s" if dev_setup else "host_setup_s"] = time.perf_counter() - t0
+            row["rank_gpu_setup" if dev_setup else "rank_host_setup"] = T.ranks[0]
+            T.close()
+        out[label] = row
+    return out
+
+
 def batch_mix_throughput(dev, stream, count=64):
     """The serving-style mix (1-D n log-uniform in [256, 16384] or 2-D n_x, n_y in [64, 1024],
     (a, b) ~ U(-0.5, 0.5), 1..16 right-hand sides), FP32: one batched forward + adjoint per
@@ -321,6 +341,12 @@ def batch_mix_throughput(dev, stream, count=64):
     many = Transform.create_many([{"n": m["n"], "a": [p[0] for p in m["ab"]], "b": [p[1] for p in m["ab"]],
                                    "eps": 1e-7} for m in mix])
     many_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    many_gpu = Transform.create_many([{"n": m["n"], "a": [p[0] for p in m["ab"]], "b": [p[1] for p in m["ab"]],
+                                       "eps": 1e-7, "setup_device": True} for m in mix])
+    many_gpu_s = time.perf_counter() - t0
+    for T in many_gpu:
+        T.close()
     saved = [T.save() for T in Ts]
     t0 = time.perf_counter()
     loaded = [Transform.load(b) for b in saved]
@@ -366,7 +392,7 @@ def batch_mix_throughput(dev, stream, count=64):
         batch.adjoint(fs, gs, stream=side)
     ms_graph = timed(graph.replay)
     out = {"members": count, "coeffs_per_step": coeffs, "plan_setup_s": setup_s,
-           "plan_setup_many_s": many_s, "plan_load_s": load_s, "saved_bytes": sum(len(b) for b in saved),
+           "plan_setup_many_s": many_s, "plan_setup_many_gpu_s": many_gpu_s, "plan_load_s": load_s, "saved_bytes": sum(len(b) for b in saved),
            "many_equals_one_by_one": same,
            "batched": {"coeffs_per_s": coeffs / (ms_batch * 1e-3), "ms_per_step": ms_batch},
            "graph_replay": {"coeffs_per_s": coeffs / (ms_graph * 1e-3), "ms_per_step": ms_graph},
@@ -586,6 +612,7 @@ def main():
 
         line["other_configs"] = other_configs(dev, stream)
         line["batch"] = batch_mix_throughput(dev, stream)
+        line["setup"] = setup_timings()
 
         if world == 1:
             line["cpu_baseline"] = oracle_throughput(nrhs)

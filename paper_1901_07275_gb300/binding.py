@@ -79,6 +79,7 @@ class Options(ctypes.Structure):
         ("fft_len_policy", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("kind", ctypes.c_int32),
+        ("setup_device", ctypes.c_int32),
     ]
 
 
@@ -157,7 +158,8 @@ def _check(status: int, what: str):
         raise JTError(status, what)
 
 
-def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None, autotune=0, kind="first") -> Options:
+def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None, autotune=0, kind="first",
+            setup_device=0) -> Options:
     o = Options()
     lib().jt_options_default(ctypes.byref(o))
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
@@ -166,6 +168,7 @@ def options(prec="fp32", nu0=27, rank_cap=0, oversample_q=3, seed=None, autotune
     o.oversample_q = oversample_q
     o.autotune = int(autotune)
     o.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+    o.setup_device = int(setup_device)
     if seed is not None:
         o.seed = seed
     return o

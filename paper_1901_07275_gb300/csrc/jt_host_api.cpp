@@ -23,6 +23,7 @@ void jt_options_default(jt_options* opt) {
     opt->fft_len_policy = 0;
     opt->autotune = 0;
     opt->kind = JT_FIRST_KIND;
+    opt->setup_device = 0;
 }
 
 const char* jt_status_string(jt_status s) {

@@ -57,6 +57,18 @@ bool valid_parameter(double v);
 void serialize_tables(const AxisTables& T, std::vector<unsigned char>& out);
 bool deserialize_tables(const unsigned char*& p, const unsigned char* end, AxisTables& T, int64_t nmax);
 
+// Recurrence coefficients of the orthonormal Jacobi polynomials, flattened for the GPU setup:
+// beta[j], sg[j], isg[j] = 1/sg[j] for j = 0..n+1, and the same in double-word as (hi, lo).
+struct SetupRec {
+    std::vector<double> beta, sg, isg, betaD, sgD, isgD;
+    double p0 = 0, sqrt_mu0 = 0;
+};
+// GPU versions of the O(n^2) setup steps (jt_setup_gpu.cu, jt_options.setup_device = 1):
+// Newton for the Gauss--Jacobi nodes from the initial angles in t (in place) with the
+// Christoffel numbers omega, and the sampled columns cl of Z = W B (n x |cl|, column-major).
+jt_status gpu_newton_nodes(const SetupRec& H, int64_t n, double maxstep, double* t, double* omega);
+jt_status gpu_columns(const SetupRec& H, const AxisTables& T, const std::vector<int>& cl, cd* out);
+
 // Upper bound on the setup threads of the calling thread (jt_plan_create_many lowers it in
 // its workers so that plans set up side by side do not oversubscribe the host).
 void set_setup_threads(int n);

@@ -296,7 +296,26 @@ double zero_guess(int64_t n, double a, double b, int64_t k) {
     return (k + 0.5 * a - 0.25) * PI / rho;
 }
 
-bool nodes_newton(const Coefs& C, double a, double b, int64_t n, std::vector<double>& t, std::vector<double>& omega) {
+SetupRec flatten(const Coefs& C) {
+    SetupRec H;
+    H.beta = C.beta;
+    H.sg = C.sg;
+    H.isg = C.isg;
+    for (size_t j = 0; j < C.betaD.size(); ++j) {
+        H.betaD.push_back(C.betaD[j].hi);
+        H.betaD.push_back(C.betaD[j].lo);
+        H.sgD.push_back(C.sgD[j].hi);
+        H.sgD.push_back(C.sgD[j].lo);
+        H.isgD.push_back(C.isgD[j].hi);
+        H.isgD.push_back(C.isgD[j].lo);
+    }
+    H.p0 = C.p0;
+    H.sqrt_mu0 = C.sqrt_mu0;
+    return H;
+}
+
+bool nodes_newton(const Coefs& C, double a, double b, int64_t n, std::vector<double>& t, std::vector<double>& omega,
+                  const SetupRec* gpu, jt_status& gpu_err) {
     const double rho = n + 0.5 * (a + b + 1.0);
     const double maxstep = 0.3 * PI / rho;
     t.resize(n);
@@ -306,6 +325,10 @@ bool nodes_newton(const Coefs& C, double a, double b, int64_t n, std::vector<dou
             t[k - 1] = zero_guess(n, a, b, k);
         else
             t[k - 1] = PI - zero_guess(n, b, a, n + 1 - k);
+    }
+    if (gpu) {
+        gpu_err = gpu_newton_nodes(*gpu, n, maxstep, t.data(), omega.data());
+        return gpu_err == JT_OK;
     }
     // blocks of consecutive nodes; end blocks in double-word
     const int BS = 32;
@@ -470,6 +493,8 @@ struct Sampler {  // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
 struct Entries {
     const AxisTables& T;
     const Coefs& C;
+    const SetupRec* gpu = nullptr;    // columns on the GPU (setup_device = 1)
+    mutable jt_status gpu_err = JT_OK;
     std::vector<cd> phase;  // e^{-2 pi i r / L}
     Entries(const AxisTables& T_, const Coefs& C_) : T(T_), C(C_) {
         phase.resize(T.L);
@@ -539,6 +564,11 @@ struct Entries {
     void cols(const std::vector<int>& cl, cd* out) const {
         const int64_t n = T.n;
         if (cl.empty()) return;
+        if (gpu) {
+            const jt_status st = gpu_columns(*gpu, T, cl, out);
+            if (st != JT_OK) gpu_err = st;
+            return;
+        }
         std::vector<int> slot(T.N, -1);
         for (size_t q = 0; q < cl.size(); ++q) slot[cl[q]] = (int)q;
         const int64_t last = T.nu0 + cl.back();
@@ -679,7 +709,7 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
     if (n < 1 || n > 65536 || !valid_parameter(a) || !valid_parameter(b)) return JT_EINVAL;
     if (!(eps > 0.0 && eps < 1.0)) return JT_EINVAL;
     if (opt.nu0 < 0 || opt.nu0 > 32 || opt.oversample_q < 1 || opt.rank_cap < 0 || opt.fft_len_policy != 0 || opt.autotune < 0 || opt.autotune > 1 ||
-        (opt.kind != JT_FIRST_KIND && opt.kind != JT_SECOND_KIND))
+        (opt.kind != JT_FIRST_KIND && opt.kind != JT_SECOND_KIND) || opt.setup_device < 0 || opt.setup_device > 1)
         return JT_EINVAL;
     if (points)
         for (int64_t k = 0; k < n; ++k)
@@ -695,6 +725,12 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
     T.nu0 = (int)std::min<int64_t>(opt.nu0, n);
     T.N = n - T.nu0;
     Coefs C(a, b, n);
+    SetupRec gpu_flat;
+    const SetupRec* gpu_rec = nullptr;
+    if (opt.setup_device == 1) {
+        gpu_flat = flatten(C);
+        gpu_rec = &gpu_flat;
+    }
     T.beta = C.beta;
     T.sg = C.sg;
     T.p0 = C.p0;
@@ -707,7 +743,9 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
             T.t.assign(1, std::acos(C.beta[0]));
             omega.assign(1, C.sqrt_mu0 * C.sqrt_mu0);
         } else {
-            bool ok = nodes_newton(C, a, b, n, T.t, omega) && nodes_valid(C, n, T.t, omega);
+            jt_status gerr = JT_OK;
+            bool ok = nodes_newton(C, a, b, n, T.t, omega, gpu_rec, gerr) && nodes_valid(C, n, T.t, omega);
+            if (gerr != JT_OK) return gerr;
             if (!ok) ok = nodes_scan(C, a, b, n, T.t, omega) && nodes_valid(C, n, T.t, omega);
             if (!ok) return JT_ENOCONV;
         }
@@ -773,6 +811,7 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
     }
 
     Entries E(T, C);
+    E.gpu = gpu_rec;
     int cap = opt.rank_cap;
     if (cap <= 0) cap = std::max<int>(64, (int)std::ceil(2.0 * std::log2((double)n)));
     cap = (int)std::min<int64_t>(cap, std::min<int64_t>(n, T.N));
@@ -784,6 +823,7 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
         std::vector<double> sig;
         bool saturated = false;
         randomized_svd(T, E, r, opt.oversample_q, rng, eps, Uk, Vk, sig, saturated);
+        if (E.gpu_err != JT_OK) return E.gpu_err;
         const int k = (int)sig.size();
         // relative error on fresh rows, always including both end rows
         std::vector<int> chk = unite(rng.pick((int)n, 24, {}), {0, (int)n - 1});

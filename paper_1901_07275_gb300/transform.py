@@ -23,7 +23,7 @@ class Transform:
     """
 
     def __init__(self, n, a, b, points=None, eps=None, precision="fp32", nu0=27, rank_cap=0,
-                 oversample_q=3, seed=None, autotune=False, kind="first", stream=None):
+                 oversample_q=3, seed=None, autotune=False, kind="first", setup_device=False, stream=None):
         import torch
 
         self.n = tuple(int(v) for v in n)
@@ -36,7 +36,7 @@ class Transform:
         self.uniform = points is None or all(p is None for p in points)
         self.kind = kind
         opt = B.options(precision, nu0=nu0, rank_cap=rank_cap, oversample_q=oversample_q, seed=seed,
-                        autotune=1 if autotune else 0, kind=kind)
+                        autotune=1 if autotune else 0, kind=kind, setup_device=1 if setup_device else 0)
         s = self._stream(stream)
         self._plan = B.jt_plan_create(self.n, self.a, self.b, points, self.eps, opt, s)
         self.info = [B.jt_plan_info(self._plan, i, self.n[i]) for i in range(self.d)]
@@ -78,7 +78,7 @@ class Transform:
             prec = sp.get("precision", "fp32")
             opt = B.options(prec, nu0=sp.get("nu0", 27), rank_cap=sp.get("rank_cap", 0),
                             oversample_q=sp.get("oversample_q", 3), seed=sp.get("seed"),
-                            kind=sp.get("kind", "first"))
+                            kind=sp.get("kind", "first"), setup_device=1 if sp.get("setup_device") else 0)
             raw.append({"n": sp["n"], "a": sp["a"], "b": sp["b"], "points": sp.get("points"),
                         "eps": sp.get("eps", _DEFAULT_EPS[prec]), "opt": opt})
         return [cls._from_handle(h) for h in B.jt_plan_create_many(raw, cls._stream(stream))]

@@ -37,7 +37,8 @@ def test_every_declared_symbol_is_exported(lib):
 def test_defaults_and_status_strings(lib):
     o = B.Options()
     lib.jt_options_default(ctypes.byref(o))
-    assert (o.prec, o.nu0, o.rank_cap, o.oversample_q, o.fft_len_policy, o.autotune, o.kind) == (0, 27, 0, 3, 0, 0, 0)
+    assert (o.prec, o.nu0, o.rank_cap, o.oversample_q, o.fft_len_policy, o.autotune, o.kind, o.setup_device) == (
+        0, 27, 0, 3, 0, 0, 0, 0)
     for s in range(7):
         assert B.status_string(s).startswith("JT_")
 
@@ -113,3 +114,20 @@ def test_plan_save_and_create_many_argument_checks(lib):
         B.jt_plan_create_many([{"n": [64], "a": [0.1], "b": [0.2]}, {"n": [64], "a": [1.5], "b": [0.2]}])
     assert e.value.status == B.JT_EINVAL
     assert lib.jt_plan_shape(None, None, None, None, None, None) == B.JT_EINVAL
+
+
+def test_gpu_setup_needs_a_device(lib):
+    """setup_device = 1 runs the O(n^2) setup steps on the GPU: without a usable device the
+    host setup entry point reports JT_ECUDA instead of falling back to the host."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    opt = B.options("fp32", setup_device=1)
+    with pytest.raises(B.JTError) as e:
+        B.AxisTables(256, 0.1, 0.2, eps=1e-7, opt=opt)
+    assert e.value.status == B.JT_ECUDA
+    opt.setup_device = 2
+    with pytest.raises(B.JTError) as e:
+        B.AxisTables(256, 0.1, 0.2, eps=1e-7, opt=opt)
+    assert e.value.status == B.JT_EINVAL
