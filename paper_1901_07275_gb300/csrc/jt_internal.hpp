@@ -67,7 +67,10 @@ struct SetupRec {
 // Newton for the Gauss--Jacobi nodes from the initial angles in t (in place) with the
 // Christoffel numbers omega, and the sampled columns cl of Z = W B (n x |cl|, column-major).
 jt_status gpu_newton_nodes(const SetupRec& H, int64_t n, double maxstep, double* t, double* omega);
-jt_status gpu_columns(const SetupRec& H, const AxisTables& T, const std::vector<int>& cl, cd* out);
+struct GpuColumns;  // device copies of the tables the column walks read, made once per setup
+GpuColumns* gpu_columns_create(const SetupRec& H, const AxisTables& T);  // nullptr on failure
+jt_status gpu_columns(GpuColumns* g, const std::vector<int>& cl, cd* out);
+void gpu_columns_destroy(GpuColumns* g);
 
 // Upper bound on the setup threads of the calling thread (jt_plan_create_many lowers it in
 // its workers so that plans set up side by side do not oversubscribe the host).

@@ -493,7 +493,7 @@ struct Sampler {  // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
 struct Entries {
     const AxisTables& T;
     const Coefs& C;
-    const SetupRec* gpu = nullptr;    // columns on the GPU (setup_device = 1)
+    GpuColumns* gpu = nullptr;        // columns on the GPU (setup_device = 1)
     mutable jt_status gpu_err = JT_OK;
     std::vector<cd> phase;  // e^{-2 pi i r / L}
     Entries(const AxisTables& T_, const Coefs& C_) : T(T_), C(C_) {
@@ -565,7 +565,7 @@ struct Entries {
         const int64_t n = T.n;
         if (cl.empty()) return;
         if (gpu) {
-            const jt_status st = gpu_columns(*gpu, T, cl, out);
+            const jt_status st = gpu_columns(gpu, cl, out);
             if (st != JT_OK) gpu_err = st;
             return;
         }
@@ -811,7 +811,15 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
     }
 
     Entries E(T, C);
-    E.gpu = gpu_rec;
+    struct ColsGuard {
+        GpuColumns* g = nullptr;
+        ~ColsGuard() { gpu_columns_destroy(g); }
+    } cols_guard;
+    if (gpu_rec) {
+        cols_guard.g = gpu_columns_create(*gpu_rec, T);
+        if (!cols_guard.g) return JT_ECUDA;
+        E.gpu = cols_guard.g;
+    }
     int cap = opt.rank_cap;
     if (cap <= 0) cap = std::max<int>(64, (int)std::ceil(2.0 * std::log2((double)n)));
     cap = (int)std::min<int64_t>(cap, std::min<int64_t>(n, T.N));

@@ -305,44 +305,89 @@ jt_status gpu_newton_nodes(const SetupRec& H, int64_t n, double maxstep, double*
     return JT_OK;
 }
 
-jt_status gpu_columns(const SetupRec& H, const AxisTables& T, const std::vector<int>& cl, cd* out) {
-    const int64_t n = T.n;
-    if (cl.empty()) return JT_OK;
-    DevBufs B;
+// Device copies of one axis's tables for the column walks, made once per setup and reused by
+// every gpu_columns call of that setup (the output buffer grows as needed).
+struct GpuColumns {
+    DevBufs bufs;
     Rec C{};
-    if (!upload_rec(B, H, C)) {
-        cudaGetLastError();
-        return JT_ECUDA;
+    ColArgs A{};
+    int* slot = nullptr;
+    double2* out = nullptr;
+    size_t out_cap = 0;
+    std::vector<int> hslot;
+    cudaStream_t stream = nullptr;
+    ~GpuColumns() {
+        if (out) cudaFree(out);
+        if (stream) cudaStreamDestroy(stream);
     }
-    std::vector<int> slot((size_t)T.N, -1);
-    for (size_t q = 0; q < cl.size(); ++q) slot[cl[q]] = (int)q;
+};
+
+GpuColumns* gpu_columns_create(const SetupRec& H, const AxisTables& T) {
+    GpuColumns* g = new GpuColumns();
+    bool ok = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess && upload_rec(g->bufs, H, g->C);
+    const int64_t n = T.n;
     std::vector<double2> phase((size_t)T.L);
     for (int64_t r = 0; r < T.L; ++r) {
         const double ang = -2.0 * PI_D * (double)r / (double)T.L;
         phase[r] = make_double2(std::cos(ang), std::sin(ang));
     }
-    ColArgs A{};
-    A.t = B.put(T.t.data(), (size_t)n);
-    A.rowP = B.put(T.rowP.data(), (size_t)n);
-    A.rowQ = B.put(T.rowQ.data(), (size_t)n);
-    A.S = B.put(T.S.data(), (size_t)n);
-    A.m = B.put(T.m.data(), (size_t)n);
-    A.phase = B.put(phase.data(), phase.size());
-    A.slot = B.put(slot.data(), slot.size());
-    A.out = B.alloc<double2>((size_t)n * cl.size());
+    ColArgs& A = g->A;
+    if (ok) {
+        A.t = g->bufs.put(T.t.data(), (size_t)n);
+        A.rowP = g->bufs.put(T.rowP.data(), (size_t)n);
+        A.rowQ = g->bufs.put(T.rowQ.data(), (size_t)n);
+        A.S = g->bufs.put(T.S.data(), (size_t)n);
+        A.m = g->bufs.put(T.m.data(), (size_t)n);
+        A.phase = g->bufs.put(phase.data(), phase.size());
+        g->slot = g->bufs.alloc<int>((size_t)T.N);
+        ok = A.t && A.rowP && A.rowQ && A.S && A.m && A.phase && g->slot;
+    }
+    A.slot = g->slot;
     A.n = (int)n;
     A.nu0 = T.nu0;
-    A.last = T.nu0 + cl.back();
     A.L = T.L;
-    if (!A.t || !A.rowP || !A.rowQ || !A.S || !A.m || !A.phase || !A.slot || !A.out) {
+    g->hslot.assign((size_t)T.N, -1);
+    if (!ok) {
+        cudaGetLastError();
+        delete g;
+        return nullptr;
+    }
+    return g;
+}
+
+void gpu_columns_destroy(GpuColumns* g) { delete g; }
+
+jt_status gpu_columns(GpuColumns* g, const std::vector<int>& cl, cd* out) {
+    if (!g) return JT_ECUDA;
+    if (cl.empty()) return JT_OK;
+    const size_t n = (size_t)g->A.n;
+    const size_t need = n * cl.size();
+    if (need > g->out_cap) {
+        if (g->out) cudaFree(g->out);
+        g->out = nullptr;
+        g->out_cap = 0;
+        if (cudaMalloc((void**)&g->out, sizeof(double2) * need) != cudaSuccess) {
+            cudaGetLastError();
+            return JT_ECUDA;
+        }
+        g->out_cap = need;
+    }
+    std::fill(g->hslot.begin(), g->hslot.end(), -1);
+    for (size_t q = 0; q < cl.size(); ++q) g->hslot[cl[q]] = (int)q;
+    ColArgs A = g->A;
+    A.out = g->out;
+    A.last = A.nu0 + cl.back();
+    static_assert(sizeof(cd) == sizeof(double2), "complex<double> and double2 share a layout");
+    const int threads = 128;
+    if (cudaMemcpyAsync(g->slot, g->hslot.data(), sizeof(int) * g->hslot.size(), cudaMemcpyHostToDevice, g->stream) !=
+        cudaSuccess) {
         cudaGetLastError();
         return JT_ECUDA;
     }
-    const int threads = 128;
-    columns_kernel<<<(unsigned)((n + threads - 1) / threads), threads>>>(C, A);
-    static_assert(sizeof(cd) == sizeof(double2), "complex<double> and double2 share a layout");
+    columns_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, g->stream>>>(g->C, A);
     if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpy(out, A.out, sizeof(double2) * (size_t)n * cl.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaMemcpyAsync(out, g->out, sizeof(double2) * need, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess) {
         cudaGetLastError();
         return JT_ECUDA;
     }

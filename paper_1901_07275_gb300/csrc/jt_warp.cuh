@@ -47,6 +47,8 @@ struct WShape {
     static constexpr int BUF0 = (XBUF > YBUF ? XBUF : YBUF);
     static constexpr int BUF = (BUF0 > X2BUF ? BUF0 : X2BUF);
     static constexpr int AUX = L + L / 32 + 1;                  // per fibre: alpha_V / g (floats)
+    // T >= 64: the step-A twiddles w_L^{t k1} (k1 = 1..15) live in shared memory, [k1-1][t]
+    static constexpr int TWS = (T >= 64) ? 15 * T : 0;           // float2
     // staging tile rows: consecutive threads cover FT fibres x (32 / FT) rows
     static constexpr int TROW = L + ((FT >= 32) ? 1 : 32 / FT);
     // gather buffer index: a half-warp writes runs m0 + [0, 8) and m0 + 128 + [0, 8)
@@ -92,13 +94,18 @@ template <int LOG2L, bool STRIDED>
 constexpr int warp_nstage() {
     using S = WShape<LOG2L>;
     if (!STRIDED) return 0;
-    return ((size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + 2 * (size_t)S::FT * S::TROW * 4 <= 112 * 1024) ? 2 : 1;
+    return ((size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)S::TWS * 8 + 2 * (size_t)S::FT * S::TROW * 4 <=
+            112 * 1024)
+               ? 2
+               : 1;
 }
+// Layout: exchange buffers [FT][BUF] float2, step-A twiddles [TWS] float2, fibre copies
+// [FT][AUX] float, staging buffers [NSTAGE][FT][TROW] float.
 template <int LOG2L>
 constexpr size_t warp_smem_bytes(bool strided) {
     using S = WShape<LOG2L>;
     const int ns = strided ? warp_nstage<LOG2L, true>() : 0;
-    return (size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)ns * S::FT * S::TROW * 4;
+    return (size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)S::TWS * 8 + (size_t)ns * S::FT * S::TROW * 4;
 }
 
 // Asynchronous 4-byte global -> shared copy (zero-filled when !valid; src must still be a
@@ -192,9 +199,11 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     const int fl = threadIdx.x / T;  // fibre slot in the CTA tile
     const int t = threadIdx.x % T;
     float2* buf = reinterpret_cast<float2*>(smem_raw) + (size_t)fl * S::BUF;
-    float* aux = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)fl * S::AUX;
+    float2* twS = reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF;
+    float* const aux0 = reinterpret_cast<float*>(twS + S::TWS);
+    float* aux = aux0 + (size_t)fl * S::AUX;
     // two staging buffers of FT x TROW floats (input of this tile and of the next one)
-    float* stage = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF) + (size_t)FT * S::AUX;
+    float* stage = aux0 + (size_t)FT * S::AUX;
 
     if constexpr (BATCHED) {
         if (njobs <= 0) return;
@@ -208,9 +217,19 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     const float2* __restrict__ ubtab = reinterpret_cast<const float2*>(A.ubtab);
 
     // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane (they depend on L only)
-    Cx<float> twA[16];
+    // (T >= 64: in shared memory instead, written here and first read after the barriers
+    // that open every tile)
+    constexpr bool TW_SMEM = S::TWS > 0;
+    Cx<float> twA[TW_SMEM ? 1 : 16];
+    if constexpr (TW_SMEM) {
+        for (int i = threadIdx.x; i < S::TWS; i += S::THREADS) {
+            const int k1 = 1 + i / T, tt = i % T;
+            twS[i] = __ldg(tw + ((tt * k1) & (L - 1)));
+        }
+    } else {
 #pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) twA[k1] = cx(__ldg(tw + ((t * k1) & (L - 1))));
+        for (int k1 = 1; k1 < 16; ++k1) twA[k1] = cx(__ldg(tw + ((t * k1) & (L - 1))));
+    }
     // Per-lane constants of one job.  Forward: padded gather-buffer index of each owned point,
     // two 16-bit fields a word.  Adjoint: whether one of the lane's bins holds more than two points.
     constexpr int NPK = FWD ? 8 : 1;
@@ -370,7 +389,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         // The exchange region is free until the rank loop and holds the results meanwhile.
         float* vres = reinterpret_cast<float*>(smem_raw);
         const float* __restrict__ auxbase =
-            reinterpret_cast<const float*>(reinterpret_cast<float2*>(smem_raw) + (size_t)FT * S::BUF);
+            aux0;
         if (SPLIT && crank != 0) {
             // rank-split partners: the dense block belongs to the first CTA of the cluster
 #pragma unroll
@@ -432,17 +451,9 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             }
 #pragma unroll
             for (int ff = 0; ff < FT; ++ff) {
-#pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) {
-                    const bool upper = (lane & off) != 0;
-#pragma unroll
-                    for (int i = 0; i < off; ++i) {
-                        const float send = upper ? part[ff][i] : part[ff][i + off];
-                        const float keep = upper ? part[ff][i + off] : part[ff][i];
-                        part[ff][i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-                    }
-                }
-                wpart[(warp * FT + ff) * 32 + lane] = part[ff][0];
+                int base = 0;
+                transpose_reduce<16, 32>(part[ff], lane, base);
+                wpart[(warp * FT + ff) * 32 + base] = part[ff][0];
             }
             __syncthreads();
             if (threadIdx.x < FT * 32) {
@@ -576,7 +587,12 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             else
                 dft16_low9<float>(x);
 #pragma unroll
-            for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], twA[k1]);
+            for (int k1 = 1; k1 < 16; ++k1) {
+                if constexpr (TW_SMEM)
+                    x[k1] = cmul(x[k1], cx(twS[(k1 - 1) * T + t]));
+                else
+                    x[k1] = cmul(x[k1], twA[k1]);
+            }
             // exchange: buf[k1][t]
             gsync<T, FT>(fl);
 #pragma unroll
