@@ -155,6 +155,19 @@ jt_status jt_forward_plain_noalloc(jt_plan* plan, const void* alpha, void* f, in
 jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_len, double* t_out,
                        double* w_out);
 
+/* Transform nrhs right-hand sides held in HOST memory: they pass through the caller's device
+ * work area dev_buf (dev_bytes bytes, at least one right-hand side) in chunks of right-hand
+ * sides, two chunks in flight on two streams the plan owns (forked from and joined back to
+ * `stream`), so that the copy to the device of one chunk, the transform of another and the copy
+ * back of a third overlap.  direction: 0 forward, 1 adjoint, 2 inverse (the rules of
+ * jt_forward, jt_adjoint, jt_inverse).  in_host and out_host hold nrhs * prod(n) elements of
+ * the plan's I/O type; page-locked host memory is needed for the copies to overlap.  The call
+ * is asynchronous on `stream`: the host arrays must stay valid, and dev_buf untouched, until
+ * the stream reaches this point.  Results equal jt_forward / jt_adjoint / jt_inverse on each
+ * chunk (each chunk gets the schedule of its own size).  JT_ENOTSUP for JT_FP64_PLAIN plans. */
+jt_status jt_transform_host(jt_plan* plan, int direction, const void* in_host, void* out_host, int64_t nrhs,
+                            void* dev_buf, size_t dev_bytes, jt_stream_t stream);
+
 /* Dimensions and options of a plan (any output pointer may be NULL): the number of axes,
  * n[0..d-1] (n[d..2] set to 1), the precision, the kind, and whether every axis uses the
  * Gauss--Jacobi nodes (so that jt_inverse is defined for the first kind). */

@@ -32,6 +32,7 @@ EXPORTS = (
     "jt_plan_info",
     "jt_destroy",
     "jt_plan_shape",
+    "jt_transform_host",
     "jt_plan_create_many",
     "jt_plan_save",
     "jt_plan_load",
@@ -112,6 +113,8 @@ def lib() -> ctypes.CDLL:
     L.jt_plan_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.jt_plan_shape.restype = i32
+    L.jt_transform_host.argtypes = [vp, i32, vp, vp, i64, vp, ctypes.c_size_t, vp]
+    L.jt_transform_host.restype = i32
     L.jt_plan_create_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(PlanDesc), vp]
     L.jt_plan_create_many.restype = i32
     L.jt_plan_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -278,6 +281,13 @@ def jt_plan_create_many(specs, stream: int = 0):
     out = (ctypes.c_void_p * max(count, 1))()
     _check(lib().jt_plan_create_many(count, out, descs, _ptr(stream)), "jt_plan_create_many")
     return [out[i] for i in range(count)]
+
+
+def jt_transform_host(plan: int, direction: int, in_ptr: int, out_ptr: int, nrhs: int, dev_ptr: int,
+                      dev_bytes: int, stream: int = 0) -> None:
+    """Transform host arrays through a device work area with overlapped copies (see jt.h)."""
+    _check(lib().jt_transform_host(_ptr(plan), int(direction), _ptr(in_ptr), _ptr(out_ptr), int(nrhs), _ptr(dev_ptr),
+                                   int(dev_bytes), _ptr(stream)), "jt_transform_host")
 
 
 def jt_plan_save(plan: int) -> bytes:

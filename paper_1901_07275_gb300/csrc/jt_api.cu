@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -56,6 +57,10 @@ struct jt_plan {
         int ksplit;
     };
     std::vector<Tuned> tuned;
+    // host-array transforms (jt_transform_host): two streams and their events, made on first use
+    std::mutex pipe_mu;
+    cudaStream_t pipe[2] = {nullptr, nullptr};
+    cudaEvent_t pipe_fork = nullptr, pipe_done[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -962,8 +967,75 @@ jt_status jt_plan_shape(const jt_plan* plan, int* d, int64_t* n, int* prec, int*
     return JT_OK;
 }
 
+jt_status jt_transform_host(jt_plan* plan, int direction, const void* in_host, void* out_host, int64_t nrhs,
+                            void* dev_buf, size_t dev_bytes, jt_stream_t stream) {
+    if (!plan || !in_host || !out_host || nrhs < 1 || !dev_buf || direction < 0 || direction > 2) return JT_EINVAL;
+    if (plan->prec == JT_FP64_PLAIN) return JT_ENOTSUP;
+    if (direction == 2 && (!plan->all_uniform || plan->kind != JT_FIRST_KIND)) return JT_ENOTSUP;
+    const int64_t per_elems = plan_elements(plan, 1);
+    if (per_elems < 1 || plan_elements(plan, nrhs) < 1) return JT_EINVAL;
+    const size_t esz = plan->prec == JT_FP32 ? 4 : 8;
+    const size_t per = (size_t)per_elems * esz;
+    const int64_t cap = (int64_t)(dev_bytes / per);  // right-hand sides the work area holds
+    if (cap < 1) return JT_EINVAL;
+    const bool fwd = direction == 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned char* src = static_cast<const unsigned char*>(in_host);
+    unsigned char* dst = static_cast<unsigned char*>(out_host);
+    unsigned char* buf = static_cast<unsigned char*>(dev_buf);
+    auto run_chunk = [&](int64_t r0, int64_t rc, unsigned char* b, cudaStream_t cs) -> jt_status {
+        const size_t bytes = (size_t)rc * per;
+        if (cudaMemcpyAsync(b, src + (size_t)r0 * per, bytes, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            return JT_ECUDA;
+        jt_status st = apply(plan, b, b, rc, fwd, cs);
+        if (st != JT_OK) return st;
+        if (cudaMemcpyAsync(dst + (size_t)r0 * per, b, bytes, cudaMemcpyDeviceToHost, cs) != cudaSuccess) return JT_ECUDA;
+        return JT_OK;
+    };
+    if (cap < 2) {  // one buffer: chunks one after another on the caller's stream
+        for (int64_t r0 = 0; r0 < nrhs; ++r0) {
+            jt_status st = run_chunk(r0, 1, buf, s);
+            if (st != JT_OK) return st;
+        }
+        return JT_OK;
+    }
+    {
+        std::lock_guard<std::mutex> lock(plan->pipe_mu);
+        for (int w = 0; w < 2; ++w) {
+            if (!plan->pipe[w] && cudaStreamCreateWithFlags(&plan->pipe[w], cudaStreamNonBlocking) != cudaSuccess)
+                return JT_ECUDA;
+            if (!plan->pipe_done[w] && cudaEventCreateWithFlags(&plan->pipe_done[w], cudaEventDisableTiming) != cudaSuccess)
+                return JT_ECUDA;
+        }
+        if (!plan->pipe_fork && cudaEventCreateWithFlags(&plan->pipe_fork, cudaEventDisableTiming) != cudaSuccess)
+            return JT_ECUDA;
+    }
+    // chunks of at most cap/2 right-hand sides, at least four of them when nrhs allows, so that
+    // the copies of one chunk overlap the transform of its neighbour
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(cap / 2, (nrhs + 3) / 4));
+    if (cudaEventRecord(plan->pipe_fork, s) != cudaSuccess) return JT_ECUDA;
+    for (int w = 0; w < 2; ++w)
+        if (cudaStreamWaitEvent(plan->pipe[w], plan->pipe_fork, 0) != cudaSuccess) return JT_ECUDA;
+    int64_t c = 0;
+    for (int64_t r0 = 0; r0 < nrhs; r0 += chunk, ++c) {
+        const int w = (int)(c & 1);
+        jt_status st = run_chunk(r0, std::min(chunk, nrhs - r0), buf + (size_t)w * (size_t)chunk * per, plan->pipe[w]);
+        if (st != JT_OK) return st;
+    }
+    for (int w = 0; w < 2; ++w) {
+        if (cudaEventRecord(plan->pipe_done[w], plan->pipe[w]) != cudaSuccess) return JT_ECUDA;
+        if (cudaStreamWaitEvent(s, plan->pipe_done[w], 0) != cudaSuccess) return JT_ECUDA;
+    }
+    return JT_OK;
+}
+
 void jt_destroy(jt_plan* plan) {
     if (!plan) return;
+    for (int w = 0; w < 2; ++w) {
+        if (plan->pipe[w]) cudaStreamDestroy(plan->pipe[w]);
+        if (plan->pipe_done[w]) cudaEventDestroy(plan->pipe_done[w]);
+    }
+    if (plan->pipe_fork) cudaEventDestroy(plan->pipe_fork);
     for (auto& ax : plan->axes) free_axis(ax);
     if (plan->plain) jt::plain_destroy(plan->plain);
     delete plan;

@@ -155,6 +155,27 @@ class Transform:
         """Inverse of :meth:`forward` (uniform axes only)."""
         return self._run(B.jt_inverse, g, out, stream)
 
+    def transform_host(self, x, out=None, direction="forward", workspace=None, stream=None):
+        """Transform a HOST tensor (pinned for overlap) through a device work area in chunks of
+        right-hand sides, copies and transforms overlapped (jt_transform_host).  ``workspace``
+        is a CUDA uint8 tensor; by default one of up to 256 MiB is allocated."""
+        import torch
+
+        if x.is_cuda or x.dtype != self.dtype or not x.is_contiguous():
+            raise TypeError("expected a contiguous host tensor of the plan's dtype")
+        if tuple(x.shape[x.dim() - self.d:]) != self.n:
+            raise ValueError(f"trailing shape {tuple(x.shape)} does not match {self.n}")
+        nrhs = math.prod(x.shape[: x.dim() - self.d]) if x.dim() > self.d else 1
+        if out is None:
+            out = torch.empty_like(x, pin_memory=x.is_pinned())
+        per = x.element_size() * math.prod(self.n)
+        if workspace is None:
+            workspace = torch.empty(max(per, min(nrhs * per, 256 << 20)), dtype=torch.uint8, device="cuda")
+        code = {"forward": 0, "adjoint": 1, "inverse": 2}[direction]
+        B.jt_transform_host(self._plan, code, x.data_ptr(), out.data_ptr(), nrhs, workspace.data_ptr(),
+                            workspace.numel(), self._stream(stream))
+        return out
+
     __call__ = forward
 
     def close(self):

@@ -96,3 +96,44 @@ def test_create_many_equals_one_by_one(torch_dev):
         assert T.ranks == R.ranks and T.save() == R.save()
         x = torch.tensor(syn.normal(920 + i, 0, tuple(sp["n"])), dtype=torch.float32, device=dev)
         assert torch.equal(T.forward(x), R.forward(x))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split"])
+@pytest.mark.parametrize("direction", ["forward", "adjoint", "inverse"])
+def test_transform_host_equals_device_transform(torch_dev, prec, direction):
+    """Host arrays through a small work area (several chunks on the two plan streams) give the
+    device transform of each right-hand side."""
+    torch, dev = torch_dev
+    from paper_1901_07275_gb300 import Transform
+
+    n = (96, 130)
+    T = Transform(n, [0.3, -0.5], [-0.4, 0.2], precision=prec)
+    x = torch.tensor(syn.normal(1600, 0, (11,) + n), dtype=T.dtype).pin_memory()
+    per = x[0].numel() * x.element_size()
+    ws = torch.empty(5 * per, dtype=torch.uint8, device=dev)  # chunks of 2 right-hand sides
+    y = T.transform_host(x, direction=direction, workspace=ws)
+    torch.cuda.synchronize()
+    fn = {"forward": T.forward, "adjoint": T.adjoint, "inverse": T.inverse}[direction]
+    for r in range(x.shape[0]):
+        ref = fn(x[r].to(dev)).cpu()
+        assert torch.allclose(y[r], ref, rtol=0, atol=1e-6 * float(ref.abs().max()))
+
+
+def test_transform_host_pageable_and_single_buffer(torch_dev):
+    torch, dev = torch_dev
+    from paper_1901_07275_gb300 import Transform
+    from paper_1901_07275_gb300 import binding as B
+
+    T = Transform((500,), [0.1], [0.2])
+    x = torch.tensor(syn.normal(1601, 0, (3, 500)), dtype=torch.float32)  # pageable
+    ws = torch.empty(500 * 4, dtype=torch.uint8, device=dev)  # room for one right-hand side
+    y = T.transform_host(x, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.allclose(y, T.forward(x.to(dev)).cpu(), rtol=0, atol=1e-6)
+    Q = Transform((64,), [0.1], [0.2], kind="second")
+    with pytest.raises(B.JTError) as e:
+        Q.transform_host(torch.zeros(64), direction="inverse")
+    assert e.value.status == B.JT_ENOTSUP
+    with pytest.raises(B.JTError) as e:
+        T.transform_host(x, workspace=torch.empty(16, dtype=torch.uint8, device=dev))
+    assert e.value.status == B.JT_EINVAL
