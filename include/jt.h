@@ -157,9 +157,9 @@ jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_le
 
 /* Transform nrhs right-hand sides held in HOST memory: they pass through the caller's device
  * work area dev_buf (dev_bytes bytes, at least one right-hand side) in chunks of right-hand
- * sides, two chunks in flight on two streams the plan owns (forked from and joined back to
- * `stream`), so that the copy to the device of one chunk, the transform of another and the copy
- * back of a third overlap.  direction: 0 forward, 1 adjoint, 2 inverse (the rules of
+ * sides, up to three chunks in flight on three streams the plan owns (forked from and joined
+ * back to `stream`), so that the copy to the device of one chunk, the transform of another and
+ * the copy back of a third overlap.  direction: 0 forward, 1 adjoint, 2 inverse (the rules of
  * jt_forward, jt_adjoint, jt_inverse).  in_host and out_host hold nrhs * prod(n) elements of
  * the plan's I/O type; page-locked host memory is needed for the copies to overlap.  The call
  * is asynchronous on `stream`: the host arrays must stay valid, and dev_buf untouched, until

@@ -57,10 +57,11 @@ struct jt_plan {
         int ksplit;
     };
     std::vector<Tuned> tuned;
-    // host-array transforms (jt_transform_host): two streams and their events, made on first use
+    // host-array transforms (jt_transform_host): three streams and their events, made on first use
+    static constexpr int PIPES = 3;
     std::mutex pipe_mu;
-    cudaStream_t pipe[2] = {nullptr, nullptr};
-    cudaEvent_t pipe_fork = nullptr, pipe_done[2] = {nullptr, nullptr};
+    cudaStream_t pipe[PIPES] = {nullptr, nullptr, nullptr};
+    cudaEvent_t pipe_fork = nullptr, pipe_done[PIPES] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -999,9 +1000,11 @@ jt_status jt_transform_host(jt_plan* plan, int direction, const void* in_host, v
         }
         return JT_OK;
     }
+    constexpr int P = jt_plan::PIPES;
+    const int np = (int)std::min<int64_t>(P, cap);  // streams (and buffers) in use
     {
         std::lock_guard<std::mutex> lock(plan->pipe_mu);
-        for (int w = 0; w < 2; ++w) {
+        for (int w = 0; w < P; ++w) {
             if (!plan->pipe[w] && cudaStreamCreateWithFlags(&plan->pipe[w], cudaStreamNonBlocking) != cudaSuccess)
                 return JT_ECUDA;
             if (!plan->pipe_done[w] && cudaEventCreateWithFlags(&plan->pipe_done[w], cudaEventDisableTiming) != cudaSuccess)
@@ -1010,19 +1013,20 @@ jt_status jt_transform_host(jt_plan* plan, int direction, const void* in_host, v
         if (!plan->pipe_fork && cudaEventCreateWithFlags(&plan->pipe_fork, cudaEventDisableTiming) != cudaSuccess)
             return JT_ECUDA;
     }
-    // chunks of at most cap/2 right-hand sides, at least four of them when nrhs allows, so that
-    // the copies of one chunk overlap the transform of its neighbour
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(cap / 2, (nrhs + 3) / 4));
+    // chunks of at most cap/np right-hand sides, at least 2 np of them when nrhs allows: chunk c
+    // runs on stream c % np with its own buffer, so that one chunk's copy in, another's
+    // transform and a third's copy out proceed together
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(cap / np, (nrhs + 2 * np - 1) / (2 * np)));
     if (cudaEventRecord(plan->pipe_fork, s) != cudaSuccess) return JT_ECUDA;
-    for (int w = 0; w < 2; ++w)
+    for (int w = 0; w < np; ++w)
         if (cudaStreamWaitEvent(plan->pipe[w], plan->pipe_fork, 0) != cudaSuccess) return JT_ECUDA;
     int64_t c = 0;
     for (int64_t r0 = 0; r0 < nrhs; r0 += chunk, ++c) {
-        const int w = (int)(c & 1);
+        const int w = (int)(c % np);
         jt_status st = run_chunk(r0, std::min(chunk, nrhs - r0), buf + (size_t)w * (size_t)chunk * per, plan->pipe[w]);
         if (st != JT_OK) return st;
     }
-    for (int w = 0; w < 2; ++w) {
+    for (int w = 0; w < np; ++w) {
         if (cudaEventRecord(plan->pipe_done[w], plan->pipe[w]) != cudaSuccess) return JT_ECUDA;
         if (cudaStreamWaitEvent(s, plan->pipe_done[w], 0) != cudaSuccess) return JT_ECUDA;
     }
@@ -1031,7 +1035,7 @@ jt_status jt_transform_host(jt_plan* plan, int direction, const void* in_host, v
 
 void jt_destroy(jt_plan* plan) {
     if (!plan) return;
-    for (int w = 0; w < 2; ++w) {
+    for (int w = 0; w < jt_plan::PIPES; ++w) {
         if (plan->pipe[w]) cudaStreamDestroy(plan->pipe[w]);
         if (plan->pipe_done[w]) cudaEventDestroy(plan->pipe_done[w]);
     }

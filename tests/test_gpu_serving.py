@@ -110,13 +110,15 @@ def test_transform_host_equals_device_transform(torch_dev, prec, direction):
     T = Transform(n, [0.3, -0.5], [-0.4, 0.2], precision=prec)
     x = torch.tensor(syn.normal(1600, 0, (11,) + n), dtype=T.dtype).pin_memory()
     per = x[0].numel() * x.element_size()
-    ws = torch.empty(5 * per, dtype=torch.uint8, device=dev)  # chunks of 2 right-hand sides
-    y = T.transform_host(x, direction=direction, workspace=ws)
-    torch.cuda.synchronize()
     fn = {"forward": T.forward, "adjoint": T.adjoint, "inverse": T.inverse}[direction]
-    for r in range(x.shape[0]):
-        ref = fn(x[r].to(dev)).cpu()
-        assert torch.allclose(y[r], ref, rtol=0, atol=1e-6 * float(ref.abs().max()))
+    # three buffers of 2 right-hand sides, and two buffers of one
+    for mult in (7, 2):
+        ws = torch.empty(mult * per, dtype=torch.uint8, device=dev)
+        y = T.transform_host(x, direction=direction, workspace=ws)
+        torch.cuda.synchronize()
+        for r in range(x.shape[0]):
+            ref = fn(x[r].to(dev)).cpu()
+            assert torch.allclose(y[r], ref, rtol=0, atol=1e-6 * float(ref.abs().max()))
 
 
 def test_transform_host_pageable_and_single_buffer(torch_dev):
