@@ -138,20 +138,45 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     std::vector<int> mtab(T.m.begin(), T.m.end());
     // bin-ordered copy of u_k for the FP32 warp kernel: [k][(s * 2 + i) * TT + t] = u_k at the
     // i-th point of bin m = t + TT s (s <= 8, i < 2), zero where the bin has fewer points
-    std::vector<Cx<R>> ubtab;
-    std::vector<int> bjtab, ovftab;
+    std::vector<Cx<R>> ubtab, ovu;
+    std::vector<int> bjtab, ovftab, ovj;
+    int ovmode = 0, ovmax = 0;
     if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
         const int64_t TT = L / 16;
         bjtab.assign((size_t)18 * TT, -1);
-        ovftab.assign((size_t)TT, 0);
+        ovftab.assign((size_t)2 * TT, 0);
+        int most = 0;  // largest number of extra points in one bin
+        for (int64_t m = 0; m <= L / 2; ++m) most = std::max(most, bin_ptr[m + 1] - bin_ptr[m] - 2);
+        ovmode = most <= 0 ? 0 : (most <= 15 ? 1 : 2);
+        std::vector<std::vector<int>> lists((size_t)TT);
         for (int64_t s2 = 0; s2 <= 8; ++s2)
             for (int64_t t = 0; t < TT; ++t) {
                 const int64_t m = t + TT * s2;
                 if (m > L / 2) continue;
                 for (int i = 0; i < 2; ++i)
                     if (bin_ptr[m] + i < bin_ptr[m + 1]) bjtab[(s2 * 2 + i) * TT + t] = bin_idx[bin_ptr[m] + i];
-                if (bin_ptr[m + 1] - bin_ptr[m] > 2) ovftab[t] = 1;
+                const int extra = std::max(0, bin_ptr[m + 1] - bin_ptr[m] - 2);
+                if (ovmode == 1) {
+                    for (int p = bin_ptr[m] + 2; p < bin_ptr[m + 1]; ++p) lists[t].push_back(bin_idx[p]);
+                    if (s2 < 8)
+                        ovftab[2 * t] |= extra << (4 * s2);
+                    else
+                        ovftab[2 * t + 1] = extra;
+                } else if (ovmode == 2 && extra > 0) {
+                    ovftab[2 * t] = 1;
+                }
             }
+        if (ovmode == 1) {
+            for (const auto& l : lists) ovmax = std::max(ovmax, (int)l.size());
+            ovj.assign((size_t)ovmax * TT, 0);
+            ovu.assign((size_t)r * ovmax * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
+            for (int64_t t = 0; t < TT; ++t)
+                for (size_t i = 0; i < lists[t].size(); ++i) {
+                    const int j = lists[t][i];
+                    ovj[i * TT + t] = j;
+                    for (int64_t k = 0; k < r; ++k) ovu[((size_t)k * ovmax + i) * TT + t] = utab[(size_t)k * n + j];
+                }
+        }
         ubtab.assign((size_t)r * 18 * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
         for (int64_t k = 0; k < r; ++k)
             for (int64_t s2 = 0; s2 <= 8; ++s2)
@@ -191,6 +216,11 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     A.bjtab = (const int*)p;
     if ((st = upload(ax, ovftab, &p, s)) != JT_OK) return st;
     A.ovftab = (const int*)p;
+    if ((st = upload(ax, ovj, &p, s)) != JT_OK) return st;
+    A.ovj = (const int*)p;
+    if ((st = upload(ax, ovu, &A.ovu, s)) != JT_OK) return st;
+    A.ovmax = ovmax;
+    A.ovmode = ovmode;
     // keep the host vectors alive until the copies are done
     if (cudaStreamSynchronize(s) != cudaSuccess) return JT_ECUDA;
     return JT_OK;

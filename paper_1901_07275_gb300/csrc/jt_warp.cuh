@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     }
     // Per-lane constants of one job.  Forward: padded gather-buffer index of each owned point,
     // two 16-bit fields a word.  Adjoint: whether one of the lane's bins holds more than two points.
-    constexpr int NPK = FWD ? 8 : 1;
+    constexpr int NPK = FWD ? 8 : 2;
     unsigned pk[NPK];
     bool sorted = false;
     auto load_job_constants = [&]() {
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 }
                 pk[i] = v[0] | (v[1] << 16);
             } else {
-                pk[i] = (unsigned)__ldg(A.ovftab + t);
+                pk[i] = (unsigned)__ldg(A.ovftab + 2 * t + i);
             }
         }
         sorted = A.sorted != 0;
@@ -564,7 +564,23 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     }
                     x[s] = z;
                 }
-                if (pk[0]) {
+                if (A.ovmode == 1 && (pk[0] | pk[1])) {
+                    // the lane's extra points, bin after bin: their indices and u_k sit in
+                    // lane-interleaved lists, so no load waits on another
+                    const float2* ouk = reinterpret_cast<const float2*>(A.ovu) + (size_t)k * A.ovmax * T;
+                    int i = 0;
+#pragma unroll
+                    for (int s = 0; s <= 8; ++s) {
+                        const int c = (s < 8) ? (int)((pk[0] >> (4 * s)) & 15u) : (int)(pk[1] & 15u);
+                        for (int q = 0; q < c; ++q, ++i) {
+                            const int j = __ldg(A.ovj + i * T + t);
+                            const float2 u = __ldg(ouk + i * T + t);
+                            const float g = aux[S::apad(j)];
+                            x[s].re = fmaf(u.x, g, x[s].re);
+                            x[s].im = fmaf(u.y, g, x[s].im);
+                        }
+                    }
+                } else if (A.ovmode == 2 && pk[0]) {
                     const float2* uk = utab + (size_t)k * n;
 #pragma unroll
                     for (int s = 0; s <= 8; ++s) {

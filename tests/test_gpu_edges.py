@@ -110,3 +110,23 @@ def test_many_right_hand_sides_ragged_tiles(torch_dev):
     x = torch.tensor(alpha, dtype=torch.float32, device=dev)
     M = [oracle.axis_matrix(m, a, b) for m, (a, b) in zip(n, ab)]
     assert rel(T.forward(x).double().cpu().numpy(), oracle.forward(alpha, M)) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("cluster", [6, 30])
+def test_nonuniform_crowded_bins(torch_dev, cluster):
+    """Nonuniform points that crowd FFT bins: up to 15 extra points a bin take the adjoint's
+    per-lane lists, more take its bin_ptr / bin_idx walk; forward and adjoint against the
+    oracle's dense J."""
+    torch, dev = torch_dev
+    n = 200
+    rng_t = np.sort(np.pi * syn.uniform(1700 + cluster, 2, (n - cluster,)))
+    # `cluster` points inside one bin of width 2 pi / 256
+    tight = 1.0 + 0.01 * syn.uniform(1701 + cluster, 2, (cluster,))
+    t = np.sort(np.concatenate([rng_t, tight]))
+    ab = [(0.25, -0.1)]
+    T = make((n,), ab, "fp32", points=[t])
+    alpha = syn.normal(1702, 0, (3, n))
+    x = torch.tensor(alpha, dtype=torch.float32, device=dev)
+    M = [oracle.axis_matrix(n, *ab[0], t)]
+    assert rel(T.forward(x).double().cpu().numpy(), oracle.forward(alpha, M)) < TOL["fp32"]
+    assert rel(T.adjoint(x).double().cpu().numpy(), oracle.adjoint(alpha, M)) < TOL["fp32"]
