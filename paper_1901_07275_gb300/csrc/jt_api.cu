@@ -158,10 +158,7 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
                 const int extra = std::max(0, bin_ptr[m + 1] - bin_ptr[m] - 2);
                 if (ovmode == 1) {
                     for (int p = bin_ptr[m] + 2; p < bin_ptr[m + 1]; ++p) lists[t].push_back(bin_idx[p]);
-                    if (s2 < 8)
-                        ovftab[2 * t] |= extra << (4 * s2);
-                    else
-                        ovftab[2 * t + 1] = extra;
+                    ovftab[2 * t] += extra;
                 } else if (ovmode == 2 && extra > 0) {
                     ovftab[2 * t] = 1;
                 }
@@ -173,7 +170,8 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
             for (int64_t t = 0; t < TT; ++t)
                 for (size_t i = 0; i < lists[t].size(); ++i) {
                     const int j = lists[t][i];
-                    ovj[i * TT + t] = j;
+                    const int s2 = (int)((T.m[j] - t) / TT);  // the lane's bin slot of point j
+                    ovj[i * TT + t] = j | (s2 << 20);
                     for (int64_t k = 0; k < r; ++k) ovu[((size_t)k * ovmax + i) * TT + t] = utab[(size_t)k * n + j];
                 }
         }

@@ -309,10 +309,10 @@ struct AxisDev {
     const void* ubtab;
     const int* bjtab;    // [(s * 2 + i) * T + t]: the point of that slot, or -1 (same layout as ubtab)
     // Points beyond the first two of a bin (FP32 warp kernel, adjoint).  ovmode 0: there are
-    // none; 1: per-lane lists, ovftab[2t], ovftab[2t+1] the counts of bins s = 0..7 (4 bits
-    // each) and s = 8, ovj[i * T + t] the i-th extra point of lane t (bins in order) and
-    // ovu[k][i * T + t] u_k there; 2: a bin holds more than 17 points, ovftab[2t] != 0 marks
-    // the lanes that walk bin_ptr / bin_idx instead.
+    // none; 1: per-lane lists, ovftab[2t] the number of extra points of lane t,
+    // ovj[i * T + t] its i-th one as j | s << 20 (s the lane's bin slot) and ovu[k][i * T + t]
+    // u_k there; 2 (a bin holds more than 17 points): ovftab[2t] != 0 marks the lanes that walk
+    // bin_ptr / bin_idx instead.
     const int* ovftab;
     const int* ovj;
     const void* ovu;

@@ -564,20 +564,33 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     }
                     x[s] = z;
                 }
-                if (A.ovmode == 1 && (pk[0] | pk[1])) {
-                    // the lane's extra points, bin after bin: their indices and u_k sit in
-                    // lane-interleaved lists, so no load waits on another
-                    const float2* ouk = reinterpret_cast<const float2*>(A.ovu) + (size_t)k * A.ovmax * T;
-                    int i = 0;
+                if (A.ovmode == 1) {
+                    // The lane's extra points in one flat loop (a warp runs as many iterations
+                    // as its busiest lane has points), their bin slot s packed with the point
+                    // index and u_k lane-interleaved, so no load waits on another.  The sums
+                    // go to the lane's own column of the exchange buffer, free until step A
+                    // once every lane of the fibre is past the previous term's step B.
+                    gsync<T, FT>(fl);
+                    const int cnt = (int)pk[0];
+                    if (cnt) {
 #pragma unroll
-                    for (int s = 0; s <= 8; ++s) {
-                        const int c = (s < 8) ? (int)((pk[0] >> (4 * s)) & 15u) : (int)(pk[1] & 15u);
-                        for (int q = 0; q < c; ++q, ++i) {
-                            const int j = __ldg(A.ovj + i * T + t);
+                        for (int s = 0; s <= 8; ++s) buf[s * T + t] = make_float2(0.0f, 0.0f);
+                        const float2* ouk = reinterpret_cast<const float2*>(A.ovu) + (size_t)k * A.ovmax * T;
+                        for (int i = 0; i < cnt; ++i) {
+                            const int e = __ldg(A.ovj + i * T + t);
                             const float2 u = __ldg(ouk + i * T + t);
+                            const int j = e & 0xfffff, s = e >> 20;
                             const float g = aux[S::apad(j)];
-                            x[s].re = fmaf(u.x, g, x[s].re);
-                            x[s].im = fmaf(u.y, g, x[s].im);
+                            float2 z = buf[s * T + t];
+                            z.x = fmaf(u.x, g, z.x);
+                            z.y = fmaf(u.y, g, z.y);
+                            buf[s * T + t] = z;
+                        }
+#pragma unroll
+                        for (int s = 0; s <= 8; ++s) {
+                            const float2 z = buf[s * T + t];
+                            x[s].re += z.x;
+                            x[s].im += z.y;
                         }
                     }
                 } else if (A.ovmode == 2 && pk[0]) {
