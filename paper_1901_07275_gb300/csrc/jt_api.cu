@@ -91,6 +91,14 @@ inline dw to_r(double v, dw*) {
 }
 
 // Build and upload the device tables of one axis in precision R.
+// Output slot o of lane t in the four-step adjoint (jt_warp.cuh, Own<>) for FFT length 2^lg.
+template <int LG>
+int own_index(int lg, int t, int o) {
+    if (lg == LG) return jt::dev::Own<LG, false>::idx(t, o);
+    if constexpr (LG > jt::F32_WARP_MIN_LOG2L) return own_index<LG - 1>(lg, t, o);
+    return 0;
+}
+
 template <class R>
 jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     const jt::AxisTables& T = ax.host;
@@ -138,11 +146,18 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     std::vector<int> mtab(T.m.begin(), T.m.end());
     // bin-ordered copy of u_k for the FP32 warp kernel: [k][(s * 2 + i) * TT + t] = u_k at the
     // i-th point of bin m = t + TT s (s <= 8, i < 2), zero where the bin has fewer points
-    std::vector<Cx<R>> ubtab, ovu;
+    std::vector<Cx<R>> ubtab, ovu, vown;
     std::vector<int> bjtab, ovftab, ovj;
     int ovmode = 0, ovmax = 0;
     if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
         const int64_t TT = L / 16;
+        // v_k in the adjoint's output order: [k][o][t] = v_k[Own(t, o)], coalesced per slot
+        vown.resize((size_t)r * 16 * TT);
+        for (int64_t k = 0; k < r; ++k)
+            for (int o = 0; o < 16; ++o)
+                for (int64_t t = 0; t < TT; ++t)
+                    vown[((size_t)k * 16 + o) * TT + t] =
+                        vtab[(size_t)k * L + own_index<jt::F32_WARP_MAX_LOG2L>(ax.log2L, (int)t, o)];
         bjtab.assign((size_t)18 * TT, -1);
         ovftab.assign((size_t)2 * TT, 0);
         int most = 0;  // largest number of extra points in one bin
@@ -212,6 +227,7 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     if ((st = upload(ax, ubtab, &A.ubtab, s)) != JT_OK) return st;
     if ((st = upload(ax, bjtab, &p, s)) != JT_OK) return st;
     A.bjtab = (const int*)p;
+    if ((st = upload(ax, vown, &A.vown, s)) != JT_OK) return st;
     if ((st = upload(ax, ovftab, &p, s)) != JT_OK) return st;
     A.ovftab = (const int*)p;
     if ((st = upload(ax, ovj, &p, s)) != JT_OK) return st;

@@ -313,6 +313,8 @@ struct AxisDev {
     // ovj[i * T + t] its i-th one as j | s << 20 (s the lane's bin slot) and ovu[k][i * T + t]
     // u_k there; 2 (a bin holds more than 17 points): ovftab[2t] != 0 marks the lanes that walk
     // bin_ptr / bin_idx instead.
+    // FP32 warp kernel, adjoint: v_k in each lane's output order, [k][o][t] = v_k[Own(t, o)]
+    const void* vown;
     const int* ovftab;
     const int* ovj;
     const void* ovu;

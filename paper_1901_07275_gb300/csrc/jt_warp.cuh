@@ -48,7 +48,7 @@ struct WShape {
     static constexpr int BUF = (BUF0 > X2BUF ? BUF0 : X2BUF);
     static constexpr int AUX = L + L / 32 + 1;                  // per fibre: alpha_V / g (floats)
     // T >= 64: the step-A twiddles w_L^{t k1} (k1 = 1..15) live in shared memory, [k1-1][t]
-    static constexpr int TWS = (T >= 64) ? 15 * T : 0;           // float2
+    static constexpr int TWS = (T >= 64) ? 15 * T + 15 * R : 0;  // float2 (+ step-B twiddles)
     // staging tile rows: consecutive threads cover FT fibres x (32 / FT) rows
     static constexpr int TROW = L + ((FT >= 32) ? 1 : 32 / FT);
     // gather buffer index: a half-warp writes runs m0 + [0, 8) and m0 + 128 + [0, 8)
@@ -128,7 +128,7 @@ struct Own {
     // number of outputs a lane holds
     static constexpr int NOUT = (T == 32) ? 16 : 16;
     // index of output slot o of lane t
-    static __device__ __forceinline__ int idx(int t, int o) {
+    static __host__ __device__ __forceinline__ int idx(int t, int o) {
         if constexpr (T == 32) {
             const int k1 = t >> 1, h = t & 1;
             return k1 + 16 * (h * 8 + (o & 7)) + (o >> 3) * (S::L / 2);  // o < 8: g = 0, o >= 8: g = 1
@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     const float* __restrict__ vblk = reinterpret_cast<const float*>(A.vblk);  // [c][0..L), zero beyond n
     const float2* __restrict__ tw = reinterpret_cast<const float2*>(A.twid);
     const float2* __restrict__ ubtab = reinterpret_cast<const float2*>(A.ubtab);
+    const float2* __restrict__ vown = reinterpret_cast<const float2*>(A.vown);
 
     // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane (they depend on L only)
     // (T >= 64: in shared memory instead, written here and first read after the barriers
@@ -222,9 +223,14 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     constexpr bool TW_SMEM = S::TWS > 0;
     Cx<float> twA[TW_SMEM ? 1 : 16];
     if constexpr (TW_SMEM) {
-        for (int i = threadIdx.x; i < S::TWS; i += S::THREADS) {
+        // [k1-1][t] = w_L^{t k1}, then the step-B twiddles [k2-1][h] = w_L^{16 h k2}
+        for (int i = threadIdx.x; i < 15 * T; i += S::THREADS) {
             const int k1 = 1 + i / T, tt = i % T;
             twS[i] = __ldg(tw + ((tt * k1) & (L - 1)));
+        }
+        for (int i = threadIdx.x; i < 15 * S::R; i += S::THREADS) {
+            const int k2 = 1 + i / S::R, hh = i % S::R;
+            twS[15 * T + i] = __ldg(tw + ((16 * hh * k2) & (L - 1)));
         }
     } else {
 #pragma unroll
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         utab = reinterpret_cast<const float2*>(A.utab);
         vblk = reinterpret_cast<const float*>(A.vblk);
         ubtab = reinterpret_cast<const float2*>(A.ubtab);
+        vown = reinterpret_cast<const float2*>(A.vown);
 #pragma unroll
         for (int i = 0; i < NPK; ++i) {
             if constexpr (FWD) {
@@ -629,9 +636,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             // adjoint: the v_k values the end of this rank term needs, fetched while step B runs
             float2 post[FWD ? 1 : 16];
             if constexpr (!FWD) {
-                const float2* vk = vtab + (size_t)k * L;
 #pragma unroll
-                for (int o = 0; o < 16; ++o) post[o] = __ldg(vk + Own<LOG2L, FWD>::idx(t, o));
+                for (int o = 0; o < 16; ++o) post[o] = __ldg(vown + ((size_t)k * 16 + o) * T + t);
             }
             gsync<T, FT>(fl);
             Cx<float> y[16];  // step-B outputs in Own<> order
@@ -680,7 +686,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 for (int q = 0; q < 16; ++q) a[q] = cx(buf[k1 * S::XROW + R * q + h]);
                 dft<16, float>(a);
 #pragma unroll
-                for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], cx(__ldg(tw + ((16 * h * k2) & (L - 1)))));
+                for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], cx(twS[15 * T + (k2 - 1) * R + h]));
                 gsync<T, FT>(fl);
 #pragma unroll
                 for (int k2 = 0; k2 < 16; ++k2) buf[S::x2idx(k1, k2, h)] = f2(a[k2]);
