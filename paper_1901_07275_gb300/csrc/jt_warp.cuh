@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                      const BatchJob* __restrict__ jobs, int njobs, long long total_tiles, const __grid_constant__ BatchPtrs ptrs) {
     using S = WShape<LOG2L>;
     constexpr int L = S::L, T = S::T, FT = S::FT;
-    constexpr bool VAL_SMEM = FWD && T >= 64;
+    constexpr bool VAL_SMEM = FWD && T >= 128;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fl = threadIdx.x / T;  // fibre slot in the CTA tile
