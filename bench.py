@@ -501,6 +501,7 @@ def main():
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
                              "peak_source": peak_src}},
         "clocks": clocks, "gpu_launches": launches,
+        "transforms_per_s": 2 * nrhs * world * args.steps / (total_ms * 1e-3),
     }
 
     if rank == 0 and not args.no_extras:

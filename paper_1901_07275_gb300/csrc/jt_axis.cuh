@@ -25,7 +25,7 @@ namespace dev {
 
 // ------------------------------------------------------------ double-word floats
 // Dekker (1971) and Joldes, Muller, Popescu (ACM TOMS 2017): TwoSum, Fast2Sum, the
-// FMA-based exact product, AccurateDWPlusDW (relative error <= 3u^2) and DWTimesDW.
+// FMA-based exact product, SloppyDWPlusDW and DWTimesDW.
 struct dw {
     float hi, lo;
 };
@@ -39,11 +39,15 @@ __device__ __forceinline__ dw fast_two_sum(float a, float b) {
     float s = a + b;
     return {s, b - (s - a)};
 }
+// Sum of two double-words by SloppyDWPlusDW (Joldes, Muller, Popescu 2017, Algorithm 5):
+// TwoSum of the high parts, the low parts added in plain FP32, one Fast2Sum (11 flops, against
+// 20 for AccurateDWPlusDW).  Its error is at most a small multiple of u^2 (|x| + |y|) rather
+// than of u^2 |x + y|: a bound relative to the operands, which is the form the error analysis
+// of an FFT (butterflies a +- w b) and of a sum over rank terms needs, so the transforms keep
+// their ~u^2 log L normwise accuracy.
 __device__ __forceinline__ dw operator+(dw x, dw y) {
     dw s = two_sum(x.hi, y.hi);
-    dw t = two_sum(x.lo, y.lo);
-    dw v = fast_two_sum(s.hi, s.lo + t.hi);
-    return fast_two_sum(v.hi, t.lo + v.lo);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
 }
 __device__ __forceinline__ dw operator-(dw x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
                     if (m <= L / 2) {
                         int p1 = __ldg(A.bin_ptr + m), p2 = __ldg(A.bin_ptr + m + 1);
                         for (int p = p1; p < p2; ++p) {
-                            int j = __ldg(A.bin_idx + p);
+                            const int j = A.sorted ? p : __ldg(A.bin_idx + p);  // sorted: identity
                             z = z + cscale(uk[j], aux[j]);
                         }
                     }
@@ -601,33 +605,53 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc[e] = acc[e] + re_mul(vk[t + T * e], x[e]);
             }
-            // dense block: alpha_c = sum_j sqrt(w_j) P~_c(t_j) g_j for c < nu0; the group
-            // reduces its partial sums through the FFT buffer (first CTA of a cluster)
+            // dense block: alpha_c = sum_j sqrt(w_j) P~_c(t_j) g_j for c < nu0 (first CTA of a
+            // cluster), DB degrees at a time: every thread's partial sums over its points go to
+            // red[i][t] in the group's FFT buffer (DB T <= 2 PADL reals), a tree over t adds them
+            // up with log2 T barriers for all DB degrees together, and element c is owned by
+            // thread c % T at e = c / T.  Groups of 512 or more threads take 8 degrees at a time
+            // (fewer barriers of the whole CTA); smaller groups one (more degrees at a time cost
+            // them registers and occupancy).
             if (!SPLIT || crank == 0) {
-                for (int c = 0; c < nu0; ++c) {
-                    R part = RealOps<R>::zero();
+                constexpr int DB0 = (T >= 512) ? 8 : 1;
+                constexpr int DB = (2 * S::PADL / T < DB0) ? 2 * S::PADL / T : DB0;
+                static_assert(DB >= 1 && DB * T <= 2 * S::PADL, "dense-block partials fit the FFT buffer");
+                R* red = sre;
+                for (int c0 = 0; c0 < nu0; c0 += DB) {
+                    R part[DB];
+#pragma unroll
+                    for (int i = 0; i < DB; ++i) part[i] = RealOps<R>::zero();
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        int j = t + T * e;
+                        const int j = t + T * e;
                         if (j < n) {
-                            if constexpr (LEAN)
-                                part = part + vblk[(size_t)c * n + j] * aux[j];
-                            else
-                                part = part + vblk[(size_t)c * n + j] * val[e];
+                            const R gj = LEAN ? aux[j] : val[e];
+#pragma unroll
+                            for (int i = 0; i < DB; ++i)
+                                if (c0 + i < nu0) part[i] = part[i] + vblk[(size_t)(c0 + i) * n + j] * gj;
                         }
                     }
-                    group_sync<T, G>(g);
-                    sre[t] = part;
+                    group_sync<T, G>(g);  // the buffer is free (last FFT pass, previous degrees)
+#pragma unroll
+                    for (int i = 0; i < DB; ++i) red[i * T + t] = part[i];
                     group_sync<T, G>(g);
                     for (int s = T / 2; s > 0; s >>= 1) {
-                        if (t < s) sre[t] = sre[t] + sre[t + s];
+                        if (t < s) {
+#pragma unroll
+                            for (int i = 0; i < DB; ++i) red[i * T + t] = red[i * T + t] + red[i * T + t + s];
+                        }
                         group_sync<T, G>(g);
                     }
-                    R tot = sre[0];
-                    // element c is owned by thread c % T at e = c / T
 #pragma unroll
-                    for (int e = 0; e < E; ++e)
-                        if (t + T * e == c) acc[e] = tot;
+                    for (int i = 0; i < DB; ++i) {
+                        const int c = c0 + i;
+                        if (c < nu0) {
+                            const R tot = red[i * T];
+#pragma unroll
+                            for (int e = 0; e < E; ++e)
+                                if (t + T * e == c) acc[e] = tot;
+                        }
+                    }
                 }
             }
         }
