@@ -403,6 +403,89 @@ def batch_mix_throughput(dev, stream, count=64):
     return out
 
 
+def batch_full_mix(dev, stream, count=512):
+    """The whole serving mix: 512 members (a fair coin between 1-D n log-uniform in
+    [256, 16384] and 2-D n_x, n_y log-uniform in [64, 1024]; (a, b) ~ U(-0.5, 0.5) per axis;
+    1..16 right-hand sides).  FP32 at eps 1e-7: plans by create_many (host setups side by side),
+    the rank split of every member's sweeps measured for its nrhs (jt_plan_tune), then one
+    batched forward + adjoint per step, eager and replayed from a CUDA graph.  Double-word
+    (split, eps 1e-12): the same for the first 64 members whose axes the split kernels take
+    (n <= 8192).  The coefficients are seeded normals drawn on the device (torch generator,
+    seed 1004 + member): at 286 M coefficients the host generator would dominate the run."""
+    import torch
+
+    from paper_1901_07275_gb300 import Batch, Transform
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    mix = syn.batch_mix(count)
+    out = {"members": count, "one_d_members": sum(len(m["n"]) == 1 for m in mix)}
+    for prec, eps, members in (("fp32", 1e-7, mix),
+                               ("split", 1e-12, [m for m in mix if max(m["n"]) <= 8192][:64])):
+        t0 = time.perf_counter()
+        Ts = Transform.create_many([{"n": m["n"], "a": [p[0] for p in m["ab"]], "b": [p[1] for p in m["ab"]],
+                                     "eps": eps, "precision": prec} for m in members])
+        setup_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for T, m in zip(Ts, members):
+            T.tune(m["nrhs"], stream=stream)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        gen = torch.Generator(device=dev)
+        xs = []
+        for i, m in enumerate(members):
+            gen.manual_seed(1004 + i)
+            xs.append(torch.randn((m["nrhs"],) + tuple(m["n"]), generator=gen, device=dev, dtype=dt))
+        fs = [torch.empty_like(x) for x in xs]
+        gs = [torch.empty_like(x) for x in xs]
+        t0 = time.perf_counter()
+        batch = Batch(Ts, [m["nrhs"] for m in members])
+        batch_s = time.perf_counter() - t0
+        coeffs = 2 * sum(x.numel() for x in xs)
+
+        def batched():
+            batch.forward(xs, fs)
+            batch.adjoint(fs, gs)
+
+        for _ in range(2):
+            batched()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            batched()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1) / reps
+        side = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            batch.forward(xs, fs, stream=side)
+            batch.adjoint(fs, gs, stream=side)
+        graph.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_graph = e0.elapsed_time(e1) / reps
+        out[prec] = {"members": len(members), "coeffs_per_step": coeffs, "eps": eps,
+                     "plan_setup_many_s": setup_s, "tune_s": tune_s, "batch_create_s": batch_s,
+                     "batched": {"coeffs_per_s": coeffs / (ms_batch * 1e-3), "ms_per_step": ms_batch,
+                                 "transforms_per_s": 2 * sum(m["nrhs"] for m in members) / (ms_batch * 1e-3)},
+                     "graph_replay": {"coeffs_per_s": coeffs / (ms_graph * 1e-3), "ms_per_step": ms_graph,
+                                      "transforms_per_s": 2 * sum(m["nrhs"] for m in members) / (ms_graph * 1e-3)}}
+        del graph
+        batch.close()
+        for T in Ts:
+            T.close()
+        del xs, fs, gs
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,6 +716,7 @@ def main():
 
         line["other_configs"] = other_configs(dev, stream)
         line["batch"] = batch_mix_throughput(dev, stream)
+        line["batch_512"] = batch_full_mix(dev, stream)
         line["setup"] = setup_timings()
 
         if world == 1:

@@ -97,3 +97,37 @@ def test_batch_rejects_mixed_precisions(torch_dev):
     with pytest.raises(B.JTError) as e:
         Batch([T3], [1])
     assert e.value.status == B.JT_ENOTSUP
+
+
+def test_batch_groups_beyond_one_launch(torch_dev):
+    """300 small 2-D members of one FFT length (L = 32) and one rank split: each stage's group
+    holds more jobs than one launch takes (256), so it runs as two launches; the batch still
+    equals the members one by one, bit for bit, and the oracle."""
+    torch, dev = torch_dev
+    from paper_1901_07275_gb300 import Batch, Transform
+
+    count = 300
+    Ts, xs, shapes = [], [], []
+    u = syn.uniform(4200, 4, (count, 4))
+    for i in range(count):
+        n = (28 + i % 5, 28 + (i // 5) % 5)
+        ab = [(float(u[i, 0] - 0.5), float(u[i, 1] - 0.5)), (float(u[i, 2] - 0.5), float(u[i, 3] - 0.5))]
+        T = Transform(n, [p[0] for p in ab], [p[1] for p in ab], precision="fp32")
+        T.set_ksplit(1)
+        Ts.append(T)
+        shapes.append((n, ab))
+        xs.append(torch.tensor(syn.normal(4200 + i, 0, (1 + i % 3,) + n), dtype=torch.float32, device=dev))
+    batch = Batch(Ts, [x.shape[0] for x in xs])
+    fb = batch.forward(xs)
+    ab_ = batch.adjoint(xs)
+    for T, x, f, a in zip(Ts, xs, fb, ab_):
+        assert torch.equal(f, T.forward(x))
+        assert torch.equal(a, T.adjoint(x))
+    for i in (0, 257, count - 1):
+        n, ab = shapes[i]
+        M = [oracle.axis_matrix(m, a, b) for m, (a, b) in zip(n, ab)]
+        ref = oracle.forward(xs[i].double().cpu().numpy(), M)
+        assert np.linalg.norm(fb[i].double().cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    batch.close()
+    for T in Ts:
+        T.close()
