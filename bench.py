@@ -303,6 +303,89 @@ def other_configs(dev, stream):
     return out
 
 
+def paper_configs(dev, stream):
+    """Two comparisons the method is judged on, beside the FP32 kernels.
+
+    1-D, n = 1024, (a, b) = (-0.25, 0.5), eps 1e-12 (1e-7 for FP32): the plain FP64 r-term FFT
+    path (cuFFT Z2Z), the double-word kernels and the FP32 kernels, forward + inverse of 1 and of
+    256 right-hand sides, each forward's relative error against the oracle's dense matrix.
+
+    3-D 256^3 with the FP32 plan's accuracy (eps 1e-7, ranks 9 a axis): one forward of one
+    right-hand side by the plain FP64 r^3 path (2^(d-1) r^3 = 2916 three-dimensional FFTs for the
+    all-high-degree block) against the FP32 fused kernels, with the relative difference of the
+    two results."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1901_07275_gb300 import Transform
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    out = {}
+    w = syn.workload("1d-1024", nrhs=256)
+    (a, b), n = w["ab"][0], w["n"][0]
+    ref = oracle.forward(w["alpha"][:1], [oracle.uniform_matrix(a, b, n)])
+    for prec, eps in (("fp64_plain", 1e-12), ("split", 1e-12), ("fp32", 1e-7)):
+        T = Transform((n,), [a], [b], eps=eps, precision=prec)
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        row = {"rank": T.ranks[0], "eps": eps}
+        for nr in (1, 256):
+            x = torch.tensor(w["alpha"][:nr], dtype=dt, device=dev)
+            f = torch.empty_like(x)
+            y = torch.empty_like(x)
+            for _ in range(2):
+                T.forward(x, out=f)
+                T.inverse(f, out=y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            e0.record(stream)
+            for _ in range(reps):
+                T.forward(x, out=f)
+                T.inverse(f, out=y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[f"{nr}_rhs"] = {"ms_per_step": ms, "coeffs_per_s": 2 * x.numel() / (ms * 1e-3)}
+            if nr == 1:
+                row["rel_err_forward"] = float(np.linalg.norm(f.double().cpu().numpy() - ref) / np.linalg.norm(ref))
+        out[f"1d-1024 {prec}"] = row
+        T.close()
+    plain = out["1d-1024 fp64_plain"]
+    for prec in ("split", "fp32"):
+        for nr in (1, 256):
+            out[f"1d-1024 {prec}"][f"speedup_over_plain_{nr}_rhs"] = (
+                plain[f"{nr}_rhs"]["ms_per_step"] / out[f"1d-1024 {prec}"][f"{nr}_rhs"]["ms_per_step"])
+
+    w = syn.workload("3d-256", nrhs=1)
+    res = {}
+    fwd = {}
+    for prec in ("fp64_plain", "fp32"):
+        T = Transform(w["n"], [p[0] for p in w["ab"]], [p[1] for p in w["ab"]], eps=1e-7, precision=prec)
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        x = torch.tensor(w["alpha"], dtype=dt, device=dev)
+        f = torch.empty_like(x)
+        T.forward(x, out=f)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 1 if prec == "fp64_plain" else 10
+        e0.record(stream)
+        for _ in range(reps):
+            T.forward(x, out=f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[prec] = {"forward_ms": ms, "coeffs_per_s": x.numel() / (ms * 1e-3), "ranks": T.ranks,
+                     "forwards_timed": reps}
+        fwd[prec] = f.double().cpu().numpy()
+        T.close()
+        del x, f
+    res["speedup_fp32_over_plain"] = res["fp64_plain"]["forward_ms"] / res["fp32"]["forward_ms"]
+    res["rel_diff_fp32_vs_plain"] = float(np.linalg.norm(fwd["fp32"] - fwd["fp64_plain"]) / np.linalg.norm(fwd["fp64_plain"]))
+    out["3d-256 forward, eps 1e-7"] = res
+    return out
+
+
 def setup_timings():
     """Plan creation time (host FP64/double-word setup, then the upload) for the longest axes,
     with the O(n^2) steps on the host cores or in FP64 kernels on the GPU (setup_device)."""
@@ -715,6 +798,7 @@ def main():
         Tq.close()
 
         line["other_configs"] = other_configs(dev, stream)
+        line["paper_configs"] = paper_configs(dev, stream)
         line["batch"] = batch_mix_throughput(dev, stream)
         line["batch_512"] = batch_full_mix(dev, stream)
         line["setup"] = setup_timings()

@@ -26,7 +26,9 @@ namespace dev {
 // ------------------------------------------------------------ double-word floats
 // Dekker (1971) and Joldes, Muller, Popescu (ACM TOMS 2017): TwoSum, Fast2Sum, the
 // FMA-based exact product, SloppyDWPlusDW and DWTimesDW.
-struct dw {
+// 8-byte aligned, so that a double-word (and, below, a complex double-word: 16 bytes) is read
+// and written with one vector access rather than one per float.
+struct __align__(8) dw {
     float hi, lo;
 };
 
@@ -96,6 +98,10 @@ __device__ __forceinline__ dw rc<dw>(double v) {
 template <class R>
 struct Cx {
     R re, im;
+};
+template <>
+struct __align__(16) Cx<dw> {
+    dw re, im;
 };
 template <class R>
 __device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) {
@@ -459,8 +465,9 @@ struct Lean {
     static constexpr bool value = Shape<R, LOG2L>::THREADS >= 1024;
 };
 
+// CTAs of 256 threads are held to 128 registers a thread, so that two of them fit an SM.
 template <class R, int LOG2L, bool FWD, bool SPLIT = false>
-__global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS)
+__global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::THREADS <= 256) ? 2 : 1)
     axis_kernel(AxisDev A, const typename RealOps<R>::io* in, typename RealOps<R>::io* out, long long nfib,
                 long long inner) {
     using S = Shape<R, LOG2L>;
