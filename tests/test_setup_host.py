@@ -177,3 +177,21 @@ def test_kind_option_is_validated():
     with pytest.raises(B.JTError) as e:
         B.AxisTables(64, 0.1, 0.2, opt=opt)
     assert e.value.status == B.JT_EINVAL
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_batch_mix_parameters_rebuild_the_weighted_matrix(k):
+    """Parameters drawn the way the serving mix draws them ((a, b) ~ U(-0.5, 0.5), n log-uniform,
+    here in [16, 600] to keep the dense oracle quick), both accuracies: the host tables rebuild
+    the oracle's W J to the requested accuracy and the points land in bins 0..L/2."""
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    u = syn.uniform(4300, 4, (8, 3))[k]
+    a, b = float(u[0] - 0.5), float(u[1] - 0.5)
+    n = int(round(np.exp(np.log(16) + u[2] * (np.log(600) - np.log(16)))))
+    eps = 1e-7 if k % 2 == 0 else 1e-12
+    T = B.AxisTables(n, a, b, eps=eps)
+    Q = oracle.uniform_matrix(a, b, n)
+    assert T.m.min() >= 0 and T.m.max() <= T.L // 2
+    err = np.linalg.norm(dense_from_tables(T) - Q) / np.linalg.norm(Q)
+    assert err < 20 * eps, (a, b, n, err)
