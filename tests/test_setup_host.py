@@ -220,3 +220,20 @@ def test_stability_quantity_2d_3d_is_of_order_1e8(row):
         w = _mode_product(w, A.T, axis)
     q = np.linalg.norm(w - v) / np.linalg.norm(v)
     assert q < 1e-7, q
+
+
+@pytest.mark.parametrize("row", read_golden("table2_rs_accuracy.txt"))
+def test_rs_accuracy_at_n_16384_matches_table_2(row):
+    """The factorised operator at n = 2^14, eps = 1e-8, on 32 sampled rows against the oracle's
+    rows of W J: a relative error of order 1e-8 like the paper's RS column of Table 2 (within
+    20 eps), including a = b = -0.9 where the paper's earlier CHEB method fails."""
+    a_b, log2n, _ = row
+    n = 2 ** int(log2n)
+    T = B.AxisTables(n, a_b, a_b, eps=1e-8)
+    rows = np.arange(7, n, n // 32)
+    ref = oracle.uniform_rows(a_b, a_b, n, rows)
+    G = T.U[:, rows].T @ T.V
+    F = np.exp(2j * np.pi * np.outer(T.m[rows], np.arange(T.nu0, n)) / T.L)
+    got = np.concatenate([T.vblk[rows], np.real(G * F)], axis=1)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 20 * 1e-8, err
