@@ -102,8 +102,9 @@ def test_B_is_non_oscillatory_in_the_chebyshev_case():
 
 @pytest.mark.parametrize("a_b,log2n,rank", [tuple(r) for r in read_golden("table1_ranks.txt")])
 def test_ranks_match_table_1(a_b, log2n, rank):
-    """RS ranks at eps = 1e-8 against Table 1.  The paper's rule for eps is not printed;
-    our spectral truncation is at most the paper's rank and within 3 of it."""
+    """RS ranks at eps = 1e-8 against Table 1 (every a = b row at n = 2^14).  The paper's
+    truncation rule for eps is not printed; our spectral truncation (sigma_k <= eps sigma_1) is
+    at most the paper's rank and within 3 of it, and equal in the Chebyshev-like rows."""
     n = 2 ** int(log2n)
     T = B.AxisTables(n, a_b, a_b, eps=1e-8)
     assert rank - 3 <= T.rank <= rank
