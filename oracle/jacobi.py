@@ -101,8 +101,14 @@ def _pn_and_derivative(x, a: float, b: float, n: int):
 
 
 def _newton_nodes(t0, a: float, b: float, n: int, iters: int = 12):
-    """Polish zeros of ``p_n(cos t)`` by Newton's method in the angle ``t``."""
+    """Polish zeros of ``p_n(cos t)`` by Newton's method in the angle ``t``.
+
+    The iteration stops once every correction is at the working precision's rounding level,
+    or once the largest relative correction no longer shrinks (it has reached the rounding
+    level of the recurrence that evaluates ``p_n``; further steps only move the nodes within
+    that level)."""
     t = _ld(t0).copy()
+    prev = None
     for _ in range(iters):
         x = np.cos(t)
         p, d, _ = _pn_and_derivative(x, a, b, n)
@@ -111,6 +117,10 @@ def _newton_nodes(t0, a: float, b: float, n: int, iters: int = 12):
         t = t + dt
         if np.all(np.abs(dt) <= 4 * np.finfo(LD).eps * np.abs(t)):
             break
+        step = float(np.max(np.abs(dt) / np.abs(t))) if t.size else 0.0
+        if prev is not None and step > 0.5 * prev:
+            break
+        prev = step
     x = np.cos(t)
     _, _, ssq = _pn_and_derivative(x, a, b, n)
     return t, x, 1 / ssq
@@ -151,9 +161,22 @@ def gauss_jacobi(a: float, b: float, n: int):
 
 
 def gauss_jacobi_nodes_at(a: float, b: float, n: int, idx):
-    """Nodes ``(t, x, omega)`` of the n-point rule at the given ascending-t indices only."""
+    """Nodes ``(t, x, omega)`` of the n-point rule at the given ascending-t indices only.
+
+    For a few indices the initial angles are the selected eigenvalues of the Jacobi matrix
+    alone (LAPACK bisection, one eigenvalue at a time: eigenvalue ``n-1-k`` in ascending x is
+    node ``k`` in ascending t); otherwise all of them.  Newton then polishes each node."""
     idx = np.asarray(idx, dtype=np.int64)
-    t0 = _golub_welsch_angles(a, b, n)[idx]
+    if n > 1 and np.unique(idx).size * 8 < n:
+        beta, sg = recurrence_coefficients(a, b, n)
+        dd, ee = beta[:n].astype(np.float64), sg[1:n].astype(np.float64)
+        t0 = np.empty(idx.size)
+        for i, k in enumerate(idx):
+            e = n - 1 - int(k)
+            xk = scipy.linalg.eigh_tridiagonal(dd, ee, eigvals_only=True, select="i", select_range=(e, e))[0]
+            t0[i] = np.arccos(np.clip(xk, -1.0, 1.0))
+    else:
+        t0 = _golub_welsch_angles(a, b, n)[idx]
     return _newton_nodes(t0, a, b, n)
 
 

@@ -110,6 +110,22 @@ def test_nodes_match_scipy_roots_jacobi(a, b, n):
     assert np.abs(omega.astype(float) / ws[order] - 1).max() < 1e-6
 
 
+@pytest.mark.parametrize("a,b", [(-0.25, 0.5), (0.9, -0.9), (-0.95, -0.6)])
+def test_selected_nodes_match_scipy_roots_jacobi(a, b):
+    """A few nodes of a long rule (initial angles from single selected eigenvalues, then
+    Newton) against scipy's nodes, including both ends of the rule."""
+    from scipy.special import roots_jacobi
+
+    n = 400
+    idx = np.array([0, 1, 57, 200, 398, 399])
+    xs, _ = roots_jacobi(n, a, b)
+    ref = np.sort(xs)[::-1][idx]  # ascending t is descending x
+    t, x, omega = oracle.gauss_jacobi_nodes_at(a, b, n, idx)
+    assert np.abs(x.astype(float) - ref).max() < 5e-15
+    _, xf, omf, _ = oracle.gauss_jacobi(a, b, n)
+    assert np.abs(omega.astype(float) / omf[idx].astype(float) - 1).max() < 1e-13
+
+
 @pytest.mark.parametrize("a,b", [(-0.25, 0.5), (0.7, 0.1)])
 def test_nodes_match_golub_welsch_eigen(a, b):
     """Nodes are the eigenvalues of the Jacobi matrix (LAPACK dense eigensolver)."""
