@@ -69,48 +69,43 @@ inline std::vector<int> qrcp_pivots(std::vector<cd> A, int m, int n, int k) {
     return perm;
 }
 
-// Orthonormal basis of the columns of the m x n matrix A (m >= n) by classical
-// Gram--Schmidt applied twice per column; returns m x n.
-inline std::vector<cd> orth(const std::vector<cd>& A, int m, int n) {
-    std::vector<cd> Q(A);
+// Orthonormal basis of the range of the m x n matrix A by classical Gram--Schmidt applied
+// twice per column; a column whose remainder is at most `drop` times the largest column norm
+// of A adds no direction and is left out.  Returns m x k, k <= n the number of columns kept.
+// (Padding the basis with arbitrary unit vectors in place of such columns would give it
+// directions concentrated on single rows, which a least-squares fit on sampled rows cannot
+// see, and the fit would then drop those rows' content.)
+inline std::vector<cd> orth(const std::vector<cd>& A, int m, int n, int& k, double drop = 1e-13) {
+    double amax = 0;
     for (int j = 0; j < n; ++j) {
-        cd* qj = &Q[(size_t)j * m];
-        double before = 0;
-        for (int i = 0; i < m; ++i) before += std::norm(qj[i]);
+        double s = 0;
+        for (int i = 0; i < m; ++i) s += std::norm(A[i + (size_t)j * m]);
+        amax = std::max(amax, std::sqrt(s));
+    }
+    std::vector<cd> Q;
+    Q.reserve(A.size());
+    k = 0;
+    std::vector<cd> q(m);
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < m; ++i) q[i] = A[i + (size_t)j * m];
         for (int pass = 0; pass < 2; ++pass) {
-            for (int l = 0; l < j; ++l) {
+            for (int l = 0; l < k; ++l) {
                 const cd* ql = &Q[(size_t)l * m];
                 cd d = 0;
-                for (int i = 0; i < m; ++i) d += std::conj(ql[i]) * qj[i];
-                for (int i = 0; i < m; ++i) qj[i] -= d * ql[i];
+                for (int i = 0; i < m; ++i) d += std::conj(ql[i]) * q[i];
+                for (int i = 0; i < m; ++i) q[i] -= d * ql[i];
             }
         }
         double nn = 0;
-        for (int i = 0; i < m; ++i) nn += std::norm(qj[i]);
+        for (int i = 0; i < m; ++i) nn += std::norm(q[i]);
         nn = std::sqrt(nn);
-        if (nn <= 1e-300 || nn <= 1e-15 * std::sqrt(before)) {
-            // numerically dependent column: replace by a unit vector orthogonal to the rest
-            for (int e = 0; e < m; ++e) {
-                for (int i = 0; i < m; ++i) qj[i] = (i == e) ? 1.0 : 0.0;
-                for (int pass = 0; pass < 2; ++pass)
-                    for (int l = 0; l < j; ++l) {
-                        const cd* ql = &Q[(size_t)l * m];
-                        cd d = 0;
-                        for (int i = 0; i < m; ++i) d += std::conj(ql[i]) * qj[i];
-                        for (int i = 0; i < m; ++i) qj[i] -= d * ql[i];
-                    }
-                nn = 0;
-                for (int i = 0; i < m; ++i) nn += std::norm(qj[i]);
-                nn = std::sqrt(nn);
-                if (nn > 0.5) break;
-            }
-        }
-        for (int i = 0; i < m; ++i) qj[i] /= nn;
+        if (!(nn > drop * amax) || nn <= 1e-300) continue;
+        for (int i = 0; i < m; ++i) Q.push_back(q[i] / nn);
+        ++k;
     }
     return Q;
 }
 
-// One-sided Jacobi (Hestenes) SVD of the m x n matrix A with m >= n:
 // A = U diag(s) V^H, U m x n with orthonormal columns, V n x n unitary,
 // s descending.  Each step rotates a column pair so that it becomes orthogonal:
 // with g = a_p^H a_q = |g| e^{i phi}, the pair (a_p, e^{-i phi} a_q) has the real

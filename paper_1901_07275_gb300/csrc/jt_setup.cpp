@@ -629,21 +629,32 @@ void randomized_svd(const AxisTables& T, const Entries& E, int r, int q, Sampler
             for (size_t c = 0; c < J.size(); ++c) Ch[c + (size_t)j * J.size()] = std::conj(Cm[j + c * (size_t)n]);
         Prow = la::qrcp_pivots(std::move(Ch), (int)J.size(), n, std::min(r, (int)J.size()));
     }
-    // step 5: orthonormal bases of Z_{:,Pcol} and Z_{Prow,:}^*
-    const int kc = (int)Pcol.size(), kr = (int)Prow.size();
-    std::vector<cd> Zc((size_t)n * kc);
-    for (int c = 0; c < kc; ++c) {
+    // step 5: orthonormal bases of Z_{:,Pcol} and Z_{Prow,:}^* (only the directions these
+    // samples really have: kc <= |Pcol|, kr <= |Prow|)
+    const int pc = (int)Pcol.size(), pr = (int)Prow.size();
+    std::vector<cd> Zc((size_t)n * pc);
+    for (int c = 0; c < pc; ++c) {
         size_t pos = std::lower_bound(J.begin(), J.end(), Pcol[c]) - J.begin();
         std::copy(Cm.begin() + pos * n, Cm.begin() + (pos + 1) * n, Zc.begin() + (size_t)c * n);
     }
-    std::vector<cd> Qcol = la::orth(Zc, n, kc);
+    // directions below this fraction of the largest sampled column are rounding noise
+    const double drop = std::max(1e-15, std::min(1e-13, 1e-2 * eps));
+    int kc = 0, kr = 0;
+    std::vector<cd> Qcol = la::orth(Zc, n, pc, kc, drop);
     std::vector<int64_t> Pr64(Prow.begin(), Prow.end());
-    std::vector<cd> rowsP((size_t)kr * N);
-    E.rows(Pr64.data(), kr, rowsP.data());
-    std::vector<cd> Zrh((size_t)N * kr);
-    for (int i = 0; i < kr; ++i)
+    std::vector<cd> rowsP((size_t)pr * N);
+    E.rows(Pr64.data(), pr, rowsP.data());
+    std::vector<cd> Zrh((size_t)N * pr);
+    for (int i = 0; i < pr; ++i)
         for (int c = 0; c < N; ++c) Zrh[c + (size_t)i * N] = std::conj(rowsP[(size_t)i * N + c]);
-    std::vector<cd> Qrow = la::orth(Zrh, N, kr);
+    std::vector<cd> Qrow = la::orth(Zrh, N, pr, kr, drop);
+    if (kc == 0 || kr == 0) {  // Z vanishes on every sample: nothing to keep
+        saturated = false;
+        sig.clear();
+        Uk.clear();
+        Vk.clear();
+        return;
+    }
     // step 6: middle matrix by least squares on fresh samples
     std::vector<int> I2 = unite(rng.pick(n, nr, Prow), Prow);
     std::vector<int> J2 = unite(rng.pick(N, ncs, Pcol), Pcol);
@@ -677,7 +688,9 @@ void randomized_svd(const AxisTables& T, const Entries& E, int r, int q, Sampler
     }
     int keep = 0;
     while (keep < kmin && s[keep] > eps * s[0] && s[keep] > 0) ++keep;
-    saturated = (keep == kmin) && kmin < std::min(n, N);  // full rank is exact, not saturated
+    // every sampled direction kept although none was left out as noise: the rank may exceed r
+    // (a full-rank Z is exact, not saturated)
+    saturated = (keep == kmin) && kc == pc && kr == pr && kmin < std::min(n, N);
     sig.assign(s.begin(), s.begin() + keep);
     Uk.assign((size_t)keep * n, cd());
     Vk.assign((size_t)keep * N, cd());

@@ -66,6 +66,34 @@ def test_uniform_tables_rebuild_the_weighted_matrix(a, b, n, eps):
     assert T.fact_err < 20 * eps
 
 
+@pytest.mark.parametrize(
+    "n,a,b",
+    [(134, 0.3882269636738198, 0.04595006974599625), (122, 0.09528870189107153, -0.1992103904429144),
+     (151, 0.3879523663189246, -0.053029945338328)],
+)
+def test_factorisation_keeps_every_row(n, a, b):
+    """Axes of the serving mix whose sampled columns are rank-deficient (24 samples, rank 8 at
+    1e-7): every row of W J is rebuilt, not only the rows the randomized sampling saw."""
+    T = B.AxisTables(n, a, b, eps=1e-7)
+    Q = oracle.uniform_matrix(a, b, n)
+    D = dense_from_tables(T)
+    row_err = np.linalg.norm(D - Q, axis=1) / np.linalg.norm(Q, axis=1)
+    assert row_err.max() < 20e-7, (row_err.argmax(), row_err.max())
+
+
+def test_serving_mix_axes_rebuild_the_weighted_matrix():
+    """The first 48 axes of the serving mix with n <= 400, at both accuracies."""
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    axes = [(n, a, b) for m in syn.batch_mix(512) for n, (a, b) in zip(m["n"], m["ab"]) if n <= 400][:48]
+    for n, a, b in axes:
+        Q = oracle.uniform_matrix(a, b, n)
+        for eps in (1e-7, 1e-12):
+            D = dense_from_tables(B.AxisTables(n, a, b, eps=eps))
+            err = np.linalg.norm(D - Q) / np.linalg.norm(Q)
+            assert err < 20 * eps, (n, a, b, eps, err)
+
+
 @pytest.mark.parametrize("a,b", [(0.25, 0.25), (-0.7, 0.6)])
 def test_nonuniform_tables_rebuild_J(a, b):
     n = 300
