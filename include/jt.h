@@ -31,8 +31,12 @@
  * synchronise.  The plan owns its device tables; all entry points are
  * thread-safe for distinct plans, and a plan is read-only after creation, so
  * concurrent calls on one plan on different streams are safe as long as their
- * output buffers do not overlap.  Input and output may be the same buffer
- * (in-place transform).  No C++ exception crosses this interface.
+ * output buffers do not overlap -- except for plans that own work buffers, whose
+ * calls must be serialised (one stream, or ordered by the caller): JT_FP64_PLAIN
+ * plans, and JT_SPLIT plans with an axis longer than 8192 (partial sums of the
+ * half-length sweeps).  Such a plan may appear only once in a batch (JT_EINVAL).
+ * Input and output may be the same buffer (in-place transform).  No C++ exception
+ * crosses this interface.
  */
 #ifndef JT_H
 #define JT_H
@@ -129,17 +133,22 @@ jt_status jt_inverse(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt
  * Forward transform of a JT_FP64_PLAIN plan that allocates nothing (the paper has no
  * counterpart; this is a library convenience).  The plain FP64 path needs work buffers
  * beyond its input and output; jt_forward takes them from the plan, this call takes them
- * from one fixed 16 MiB device array compiled into libjt, which every GPU that loads the
- * library holds until the process exits.  It is meant for callers that must not request
- * device memory at call time: a serving loop that cannot risk an allocation failure or the
- * allocator's locks in the middle of a request, or a process whose free device memory is
- * already reserved by another allocator (a framework's caching allocator, for instance).
+ * from one fixed 16 MiB device array compiled into libjt.  It is meant for callers that must
+ * not request device memory at call time: a serving loop that cannot risk an allocation
+ * failure or the allocator's locks in the middle of a request, or a process whose free device
+ * memory is already reserved by another allocator (a framework's caching allocator, for
+ * instance).
  *   Same arguments, layout and result as jt_forward (float64 in and out, device pointers).
- *   JT_ENOTSUP for plans of another precision; JT_EINVAL for bad arguments or when the plan
- *   needs more than 16 MiB of work space (about 2^18 points, e.g. 512 x 512 fits,
- *   1024 x 1024 does not).  No cudaMalloc, cudaFree or allocating library call is made.
- *   The first call on a device looks up the array's device address (with that device
- *   current) and caches it; make that first call before any stream capture.
+ *   JT_ENOTSUP for plans of another precision; JT_EINVAL for bad arguments (the element
+ *   limit of jt_forward included) or when the plan needs more work space than the array
+ *   holds.  With L_a the FFT length of axis a (jt_plan_info: n_a rounded up to a power of
+ *   two) and N = prod_a n_a, the plan needs
+ *       R(16 prod_a L_a) + R(16 max_a (N / n_a) L_a) + 2 R(8 N)  <=  16 MiB,
+ *   R(x) = x rounded up to a multiple of 256 bytes.  512 x 512 fits (12 MiB); 513 x 513 and
+ *   1024 x 1024 do not.  No cudaMalloc, cudaFree or allocating library call is made.
+ *   The array's device address is looked up when the plan is created, on the plan's device;
+ *   that lookup also loads the module, so the device commits the 16 MiB when its first
+ *   JT_FP64_PLAIN plan is created (not inside this call) and holds them until exit.
  *   Every call shares the one array, which keeps the last call's contents (each call clears
  *   what it needs at zero itself): calls that overlap on the GPU -- on different streams, or
  *   from different host threads -- race on it and must be serialised by the caller.
@@ -257,8 +266,8 @@ typedef struct jt_batch jt_batch;
  * (see jt_plan_schedule; measured first for plans created with autotune = 1); sweeps with
  * different splits go to different launches.  The launches of one stage are spread over
  * four worker streams that the batch owns, forked from and joined back to the caller's
- * stream on every execution.  JT_EINVAL for mixed precisions or bad arguments, JT_ENOTSUP
- * for JT_FP64_PLAIN plans. */
+ * stream on every execution.  JT_EINVAL for mixed precisions, bad arguments, or a JT_SPLIT
+ * plan with an axis longer than 8192 listed twice; JT_ENOTSUP for JT_FP64_PLAIN plans. */
 jt_status jt_batch_create(jt_batch** out, int count, jt_plan* const* plans, const int64_t* nrhs,
                           jt_stream_t stream);
 
@@ -273,6 +282,17 @@ void jt_batch_destroy(jt_batch* batch);
 
 /* Static string naming a status code. */
 const char* jt_status_string(jt_status s);
+
+/* Measurement helper (no counterpart in the paper): the FP32 arithmetic rate that bounds the
+ * axis kernels, measured instead of derived from unit counts.  Launches, on `stream`, a
+ * persistent grid of 4 CTAs of 256 threads per SM in which every thread runs 8 independent
+ * chains of 16 * iters fused multiply-adds: fma.rn.f32 (paired = 0) or fma.rn.f32x2, two FMAs
+ * an instruction (paired = 1).  The caller times the launch (events on `stream`).
+ *   sink: device float32 array of at least sink_len >= 1024 * SM-count elements (written);
+ *   *flops (host): the launch's floating-point operations, 2 per FMA.
+ *   JT_EINVAL for iters < 1, a NULL pointer or a short sink; JT_ECUDA on a launch error. */
+jt_status jt_probe_fp32_fma(int paired, int64_t iters, float* sink, int64_t sink_len, double* flops,
+                            jt_stream_t stream);
 
 /* ------------------------------------------------------------------------------------
  * Host-side setup of one axis, for inspection and testing of the plan tables.  Runs the

@@ -44,6 +44,7 @@ EXPORTS = (
     "jt_batch_adjoint",
     "jt_batch_destroy",
     "jt_status_string",
+    "jt_probe_fp32_fma",
     "jt_axis_tables_create",
     "jt_axis_tables_info",
     "jt_axis_tables_copy",
@@ -137,6 +138,8 @@ def lib() -> ctypes.CDLL:
     L.jt_batch_destroy.restype = None
     L.jt_status_string.argtypes = [i32]
     L.jt_status_string.restype = ctypes.c_char_p
+    L.jt_probe_fp32_fma.argtypes = [i32, i64, vp, i64, ctypes.POINTER(dbl), vp]
+    L.jt_probe_fp32_fma.restype = i32
     L.jt_axis_tables_create.argtypes = [ctypes.POINTER(vp), i64, dbl, dbl, vp, dbl, ctypes.POINTER(Options)]
     L.jt_axis_tables_create.restype = i32
     L.jt_axis_tables_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
@@ -150,6 +153,14 @@ def lib() -> ctypes.CDLL:
     L.jt_axis_tables_destroy.restype = None
     _lib = L
     return L
+
+
+def jt_probe_fp32_fma(paired: bool, iters: int, sink_ptr: int, sink_len: int, stream: int = 0) -> float:
+    """Launch the FP32 FMA-rate probe on `stream`; returns the launch's flops."""
+    flops = ctypes.c_double(0.0)
+    _check(lib().jt_probe_fp32_fma(1 if paired else 0, int(iters), ctypes.c_void_p(sink_ptr), int(sink_len),
+                                   ctypes.byref(flops), ctypes.c_void_p(stream)), "jt_probe_fp32_fma")
+    return flops.value
 
 
 def status_string(status: int) -> str:
