@@ -863,7 +863,9 @@ jt_status axis_setup(AxisTables& T, int64_t n, double a, double b, const double*
         double err = (den > 0) ? std::sqrt(num / den) : 0.0;
         bool ok = !saturated && err <= tol;
         if (ok || r >= cap) {
-            if (!ok && saturated) return JT_ENOCONV;
+            // at the cap, the sampled check decides: a rank that reaches eps on it is kept even
+            // if every sampled direction was kept; one that misses it is not convergence
+            if (!(err <= tol)) return JT_ENOCONV;
             T.rank = k;
             T.U.swap(Uk);
             T.V.swap(Vk);

@@ -132,10 +132,13 @@ def test_B_is_non_oscillatory_in_the_chebyshev_case():
 def test_ranks_match_table_1(a_b, log2n, rank):
     """RS ranks at eps = 1e-8 against Table 1 (every a = b row at n = 2^14).  The paper's
     truncation rule for eps is not printed; our spectral truncation (sigma_k <= eps sigma_1) is
-    at most the paper's rank and within 3 of it, and equal in the Chebyshev-like rows."""
+    at most the paper's rank and within 3 of it, and equal to it in the Chebyshev-like rows
+    a = b = 0.5 and a = b = -0.5 (ranks 9 and 2)."""
     n = 2 ** int(log2n)
     T = B.AxisTables(n, a_b, a_b, eps=1e-8)
     assert rank - 3 <= T.rank <= rank
+    if abs(a_b) == 0.5:
+        assert T.rank == rank
 
 
 @pytest.mark.parametrize("row", read_golden("stability_table.txt"))
@@ -152,6 +155,20 @@ def test_stability_quantity_matches_table(row):
         v = rng.standard_normal(n)
         worst = max(worst, np.linalg.norm(A.T @ (A @ v) - v) / np.linalg.norm(v))
     assert worst < max(20 * val * 1e-8, 2e-9), worst
+
+
+def test_rank_cap_below_the_needed_rank_is_reported():
+    """A rank cap below the rank the accuracy needs is JT_ENOCONV (the rank-adaptive wrapper of
+    Sec. 2.1 cannot reach eps), both from the host tables and from plan creation, which stops
+    in its host setup before any device work."""
+    with pytest.raises(B.JTError) as e:
+        B.AxisTables(512, 0.1, -0.2, eps=1e-12, opt=B.options(rank_cap=2))
+    assert e.value.status == B.JT_ENOCONV
+    with pytest.raises(B.JTError) as e:
+        B.jt_plan_create([512], [0.1], [-0.2], None, 1e-12, B.options("fp32", rank_cap=2))
+    assert e.value.status == B.JT_ENOCONV
+    # the same cap is enough at a coarse accuracy of a Chebyshev-like axis (rank 2)
+    assert B.AxisTables(512, -0.5, -0.5, eps=1e-8, opt=B.options(rank_cap=2)).rank <= 2
 
 
 def test_factorisation_is_deterministic_and_seeded():
