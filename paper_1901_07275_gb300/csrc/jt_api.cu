@@ -32,6 +32,7 @@ using jt::dev::dw;
 struct DeviceAxis {
     jt::AxisTables host;
     AxisDev dev{};
+    jt::dev::BigAxisDev big{};  // double-word axes of length 2^14 only
     int log2L = 0;
     std::vector<void*> allocs;
 };
@@ -99,6 +100,14 @@ int own_index(int lg, int t, int o) {
     return 0;
 }
 
+// Forward output slot c of the four-step kernel (jt_warp.cuh, fslot<>) for FFT length 2^lg.
+template <int LG>
+int fslot_index(int lg, int c) {
+    if (lg == LG) return jt::dev::fslot<LG>(c);
+    if constexpr (LG > jt::F32_WARP_MIN_LOG2L) return fslot_index<LG - 1>(lg, c);
+    return 0;
+}
+
 template <class R>
 jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     const jt::AxisTables& T = ax.host;
@@ -146,9 +155,9 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     std::vector<int> mtab(T.m.begin(), T.m.end());
     // bin-ordered copy of u_k for the FP32 warp kernel: [k][(s * 2 + i) * TT + t] = u_k at the
     // i-th point of bin m = t + TT s (s <= 8, i < 2), zero where the bin has fewer points
-    std::vector<Cx<R>> ubtab, ovu, vown;
-    std::vector<int> bjtab, ovftab, ovj;
-    int ovmode = 0, ovmax = 0;
+    std::vector<Cx<R>> ubtab, ovu, vown, fbtab;
+    std::vector<int> bjtab, ovftab, ovj, bjf;
+    int ovmode = 0, ovmax = 0, fbin = 0;
     if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
         const int64_t TT = L / 16;
         // v_k in the adjoint's output order: [k][o][t] = v_k[Own(t, o)], coalesced per slot
@@ -189,6 +198,35 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
                     ovj[i * TT + t] = j | (s2 << 20);
                     for (int64_t k = 0; k < r; ++k) ovu[((size_t)k * ovmax + i) * TT + t] = utab[(size_t)k * n + j];
                 }
+        }
+        // forward in bin order (no bin with more than two points): the points of the output
+        // bins each lane keeps after step B, and u_k there; every point must appear once
+        if (ovmode == 0) {
+            bjf.assign((size_t)18 * TT, -1);
+            std::vector<int> seen(n, 0);
+            for (int64_t t = 0; t < TT; ++t)
+                for (int c = 0; c < 9; ++c) {
+                    if (c == 8 && t != 0) continue;
+                    const int64_t m = own_index<jt::F32_WARP_MAX_LOG2L>(ax.log2L, (int)t,
+                                                                        fslot_index<jt::F32_WARP_MAX_LOG2L>(ax.log2L, c));
+                    if (m > L / 2) continue;
+                    for (int i = 0; i < 2 && bin_ptr[m] + i < bin_ptr[m + 1]; ++i) {
+                        const int j = bin_idx[bin_ptr[m] + i];
+                        bjf[(size_t)(2 * c + i) * TT + t] = j;
+                        seen[j]++;
+                    }
+                }
+            fbin = 1;
+            for (int64_t j = 0; j < n; ++j)
+                if (seen[j] != 1) fbin = 0;
+            if (fbin) {
+                fbtab.assign((size_t)r * 18 * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
+                for (int64_t k = 0; k < r; ++k)
+                    for (size_t q = 0; q < bjf.size(); ++q)
+                        if (bjf[q] >= 0) fbtab[(size_t)k * 18 * TT + q] = utab[(size_t)k * n + bjf[q]];
+            } else {
+                bjf.clear();
+            }
         }
         ubtab.assign((size_t)r * 18 * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
         for (int64_t k = 0; k < r; ++k)
@@ -235,6 +273,72 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     if ((st = upload(ax, ovu, &A.ovu, s)) != JT_OK) return st;
     A.ovmax = ovmax;
     A.ovmode = ovmode;
+    if ((st = upload(ax, fbtab, &A.fbtab, s)) != JT_OK) return st;
+    if ((st = upload(ax, bjf, &p, s)) != JT_OK) return st;
+    A.bjf = (const int*)p;
+    A.fbin = fbin;
+    // Double-word axes of length 2^14: the tables of the two half-length transforms
+    // (jt_axis_dw_big.cu): u_k e^{2 pi i m_j / L}, bins m_j mod L/2 and their CSR, the
+    // half-length twiddles, and the partial-sum buffer of one launch.
+    std::vector<Cx<R>> utab1, tw2;
+    std::vector<int> mtab2, bin_ptr2, bin_idx2;
+    if (std::is_same<R, dw>::value && ax.log2L == jt::MAX_LOG2L_DW) {
+        const int64_t Lh = L / 2;
+        utab1.resize((size_t)r * n);
+        for (int64_t k = 0; k < r; ++k)
+            for (int64_t j = 0; j < n; ++j) {
+                const size_t i = (size_t)k * n + j;
+                const jt::cd u = second ? jt::cd(T.U[i].imag(), -T.U[i].real()) : T.U[i];
+                const double ang = twopi * (double)T.m[j] / (double)L;
+                const jt::cd v = u * jt::cd(std::cos(ang), std::sin(ang));
+                utab1[i] = Cx<R>{to_r(v.real(), tag), to_r(v.imag(), tag)};
+            }
+        tw2.resize(Lh);
+        for (int64_t q = 0; q < Lh; ++q) {
+            const double ang = twopi * (double)q / (double)Lh;
+            tw2[q] = Cx<R>{to_r(std::cos(ang), tag), to_r(std::sin(ang), tag)};
+        }
+        mtab2.resize(n);
+        bin_ptr2.assign(Lh + 1, 0);
+        bin_idx2.resize(n);
+        for (int64_t j = 0; j < n; ++j) {
+            mtab2[j] = (int)(T.m[j] % Lh);
+            bin_ptr2[mtab2[j] + 1]++;
+        }
+        for (int64_t m = 0; m < Lh; ++m) bin_ptr2[m + 1] += bin_ptr2[m];
+        std::vector<int> fill(bin_ptr2.begin(), bin_ptr2.end() - 1);
+        for (int64_t j = 0; j < n; ++j) bin_idx2[fill[mtab2[j]]++] = (int)j;
+        jt::dev::BigAxisDev& Bg = ax.big;
+        Bg.n = (int)n;
+        Bg.nu0 = (int)nu0;
+        Bg.rank = (int)r;
+        Bg.vtab = reinterpret_cast<const Cx<dw>*>(A.vtab);
+        Bg.utab = reinterpret_cast<const Cx<dw>*>(A.utab);
+        Bg.vblk = reinterpret_cast<const dw*>(A.vblk);
+        if ((st = upload(ax, utab1, &p, s)) != JT_OK) return st;
+        Bg.utab1 = reinterpret_cast<const Cx<dw>*>(p);
+        if ((st = upload(ax, tw2, &p, s)) != JT_OK) return st;
+        Bg.tw2 = reinterpret_cast<const Cx<dw>*>(p);
+        if ((st = upload(ax, mtab2, &p, s)) != JT_OK) return st;
+        Bg.mtab2 = (const int*)p;
+        if ((st = upload(ax, bin_ptr2, &p, s)) != JT_OK) return st;
+        Bg.bin_ptr2 = (const int*)p;
+        if ((st = upload(ax, bin_idx2, &p, s)) != JT_OK) return st;
+        Bg.bin_idx2 = (const int*)p;
+        int dev_id = 0, sms = 0;
+        if (cudaGetDevice(&dev_id) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess)
+            return JT_ECUDA;
+        Bg.max_ctas = std::max(1, sms);
+        void* part = nullptr;
+        if (cudaMalloc(&part, sizeof(dw) * (size_t)Bg.max_ctas * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            return JT_ENOMEM;
+        }
+        ax.allocs.push_back(part);
+        Bg.part = reinterpret_cast<dw*>(part);
+        if (jt::dw_big_init() != cudaSuccess) return JT_ECUDA;
+    }
     // keep the host vectors alive until the copies are done
     if (cudaStreamSynchronize(s) != cudaSuccess) return JT_ECUDA;
     return JT_OK;
@@ -261,6 +365,8 @@ cudaError_t launch_sweep(const jt_plan* plan, int ax, bool fwd, const void* src,
     const DeviceAxis& A = plan->axes[ax];
     if (plan->prec == JT_FP32)
         return jt::launch_axis_f32(A.dev, A.log2L, fwd, (const float*)src, (float*)dst, nfib, inner, ksplit, s);
+    if (A.log2L > jt::DW_SMEM_MAX_LOG2L)
+        return jt::launch_axis_dw_big(A.big, fwd, (const double*)src, (double*)dst, nfib, inner, s);
     return jt::launch_axis_dw(A.dev, A.log2L, fwd, (const double*)src, (double*)dst, nfib, inner, ksplit, s);
 }
 
@@ -538,6 +644,15 @@ jt_status jt_batch_create(jt_batch** out, int count, jt_plan* const* plans, cons
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || nrhs[i] < 1) return JT_EINVAL;
         if (plans[i]->prec != prec) return JT_EINVAL;
+    }
+    // a plan whose sweeps use a work buffer of its own (double-word axes of length 2^14) may
+    // appear once: the workers would otherwise run two of its sweeps on that buffer at once
+    for (int i = 0; i < count; ++i) {
+        bool own_work = false;
+        for (const auto& ax : plans[i]->axes) own_work = own_work || (prec == JT_SPLIT && ax.log2L > jt::DW_SMEM_MAX_LOG2L);
+        if (!own_work) continue;
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return JT_EINVAL;
     }
     jt_batch* b = nullptr;
     try {
@@ -949,6 +1064,7 @@ jt_status jt_inverse(jt_plan* plan, const void* g, void* alpha, int64_t nrhs, jt
 jt_status jt_forward_plain_noalloc(jt_plan* plan, const void* alpha, void* f, int64_t nrhs, jt_stream_t stream) {
     if (!plan || !alpha || !f || nrhs < 1) return JT_EINVAL;
     if (plan->prec != JT_FP64_PLAIN) return JT_ENOTSUP;
+    if (plan_elements(plan, nrhs) < 1) return JT_EINVAL;
     return jt::plain_apply_static(plan->plain, (const double*)alpha, (double*)f, nrhs, true, (cudaStream_t)stream);
 }
 

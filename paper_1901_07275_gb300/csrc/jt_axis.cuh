@@ -138,6 +138,54 @@ template <class R>
 __device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
     return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
+// Double-word operations inside the FFT without the final renormalisation: TwoSum of the high
+// parts with the low parts added in FP32 (8 operations against 11), and the FMA-based product
+// without its lo x lo term (5 operations against 9).  The result is an unevaluated sum hi + lo
+// whose lo may exceed half an ulp of hi; TwoSum and the FMA error term stay exact for such
+// inputs, so the rounding left is that of the FP32 low parts (a few u^2 of the values).  Every
+// DFT renormalises its outputs once (Fast2Sum), and a twiddle product or a scaling feeds a DFT.
+__device__ __forceinline__ dw add_nr(dw x, dw y) {
+    const dw s = two_sum(x.hi, y.hi);
+    return {s.hi, s.lo + (x.lo + y.lo)};
+}
+__device__ __forceinline__ dw sub_nr(dw x, dw y) { return add_nr(x, dw{-y.hi, -y.lo}); }
+__device__ __forceinline__ dw mul_nr(dw x, dw y) {
+    const float ch = x.hi * y.hi;
+    const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+    const float cl2 = __fmaf_rn(x.lo, y.hi, x.hi * y.lo);
+    return {ch, cl1 + cl2};
+}
+__device__ __forceinline__ dw renorm(dw x) { return fast_two_sum(x.hi, x.lo); }
+__device__ __forceinline__ Cx<dw> cmul(Cx<dw> a, Cx<dw> b) {
+    return {sub_nr(mul_nr(a.re, b.re), mul_nr(a.im, b.im)), add_nr(mul_nr(a.re, b.im), mul_nr(a.im, b.re))};
+}
+__device__ __forceinline__ Cx<dw> cscale(Cx<dw> a, dw s) { return {mul_nr(a.re, s), mul_nr(a.im, s)}; }
+
+// Butterfly sums and the products of the constant twiddles inside a DFT (unnormalised for
+// double-words).
+template <class R>
+__device__ __forceinline__ Cx<R> bf_add(Cx<R> a, Cx<R> b) {
+    return a + b;
+}
+template <class R>
+__device__ __forceinline__ Cx<R> bf_sub(Cx<R> a, Cx<R> b) {
+    return a - b;
+}
+__device__ __forceinline__ Cx<dw> bf_add(Cx<dw> a, Cx<dw> b) { return {add_nr(a.re, b.re), add_nr(a.im, b.im)}; }
+__device__ __forceinline__ Cx<dw> bf_sub(Cx<dw> a, Cx<dw> b) { return {sub_nr(a.re, b.re), sub_nr(a.im, b.im)}; }
+template <class R>
+__device__ __forceinline__ Cx<R> h_rot(Cx<R> v, R h) {  // ((re - im) h, (re + im) h)
+    return {(v.re - v.im) * h, (v.re + v.im) * h};
+}
+__device__ __forceinline__ Cx<dw> h_rot(Cx<dw> v, dw h) {
+    return {mul_nr(sub_nr(v.re, v.im), h), mul_nr(add_nr(v.re, v.im), h)};
+}
+template <class R>
+__device__ __forceinline__ void dft_out(Cx<R>* a, int n) {}
+__device__ __forceinline__ void dft_out(Cx<dw>* a, int n) {
+    for (int i = 0; i < n; ++i) a[i] = Cx<dw>{renorm(a[i].re), renorm(a[i].im)};
+}
+
 template <class R>
 __device__ __forceinline__ Cx<R> mul_i(Cx<R> a) {  // multiply by +i
     return {-a.im, a.re};
@@ -167,7 +215,7 @@ __device__ __forceinline__ Cx<R> twc(Cx<R> v) {
     } else if constexpr (8 * k == N || 8 * k == 3 * N || 8 * k == 5 * N || 8 * k == 7 * N) {
         const R h = rc<R>(0.70710678118654752440084436210484903928);
         // (1 + i)/sqrt2 rotated by the multiple of i
-        Cx<R> r{(v.re - v.im) * h, (v.re + v.im) * h};
+        Cx<R> r = h_rot(v, h);
         if constexpr (8 * k == N) return r;
         if constexpr (8 * k == 3 * N) return mul_i(r);
         if constexpr (8 * k == 5 * N) return {-r.re, -r.im};
@@ -217,8 +265,8 @@ template <int LEN, int HALF, int K, class R>
 __device__ __forceinline__ void dft_stage_k(Cx<R>* t, int i) {
     Cx<R> u = t[i + K];
     Cx<R> v = twc<K, LEN, R>(t[i + K + HALF]);
-    t[i + K] = u + v;
-    t[i + K + HALF] = u - v;
+    t[i + K] = bf_add(u, v);
+    t[i + K + HALF] = bf_sub(u, v);
 }
 
 template <int LEN, int R, class Rt>
@@ -273,6 +321,7 @@ __device__ __forceinline__ void dft(Cx<Rt>* a) {
         if constexpr (R >= 4) dft_stage<4, R, Rt>(t);
         if constexpr (R >= 8) dft_stage<8, R, Rt>(t);
         if constexpr (R >= 16) dft_stage<16, R, Rt>(t);
+        dft_out(t, R);
 #pragma unroll
         for (int i = 0; i < R; ++i) a[i] = t[i];
     }
@@ -299,8 +348,43 @@ struct Shape {
     static constexpr int THREADS = G * T;
     static constexpr int P = (LOG2L <= LG) ? 1 : (LOG2L + LG - 1) / LG;  // Stockham passes
     static constexpr int R0 = 1 << (LOG2L - LG * (P - 1));               // radix of the first pass
-    static constexpr int PADL = L + (L >> 5) + 1;                     // padded complex buffer
-    static __host__ __device__ constexpr int pad(int i) { return i + (i >> 5); }
+    // FP32: separate re / im arrays of L + L/32 + 1 floats, one word of padding per 32.
+    // Double-word: one array of complex double-words (16 bytes), one entry of padding per 8, so
+    // that the 8 lanes of a quarter-warp touch 8 different 16-byte bank groups in every pass.
+    static constexpr bool CPLX = sizeof(R) == 8;
+    static constexpr int PADL = CPLX ? L + (L >> 3) + 1 : L + (L >> 5) + 1;
+    static __host__ __device__ constexpr int pad(int i) { return CPLX ? i + (i >> 3) : i + (i >> 5); }
+    // per group: the exchange buffer (2 PADL reals), then L reals of fibre data, kept even
+    static constexpr int GSTRIDE = ((2 * PADL + L) + 1) & ~1;
+};
+
+// The exchange buffer of one group: (re, im) arrays for FP32, interleaved complex double-words.
+template <class R>
+struct XBuf {
+    R* re;
+    R* im;
+    template <class S>
+    __device__ __forceinline__ void put(int i, Cx<R> v) const {
+        re[S::pad(i)] = v.re;
+        im[S::pad(i)] = v.im;
+    }
+    template <class S>
+    __device__ __forceinline__ Cx<R> get(int i) const {
+        return Cx<R>{re[S::pad(i)], im[S::pad(i)]};
+    }
+};
+template <>
+struct XBuf<dw> {
+    dw* re;  // start of the buffer: Cx<dw>[PADL]
+    dw* im;  // unused
+    template <class S>
+    __device__ __forceinline__ void put(int i, Cx<dw> v) const {
+        reinterpret_cast<Cx<dw>*>(re)[S::pad(i)] = v;
+    }
+    template <class S>
+    __device__ __forceinline__ Cx<dw> get(int i) const {
+        return reinterpret_cast<const Cx<dw>*>(re)[S::pad(i)];
+    }
 };
 
 // Tables of one axis on the device (all owned by the plan).
@@ -329,6 +413,28 @@ struct AxisDev {
     const int* ovj;
     const void* ovu;
     int ovmax, ovmode;
+    // FP32 warp kernel, forward, when no bin holds more than two points (fbin = 1): u_k at the
+    // points of each lane's output bins after step B, [k][(c * 2 + i) * T + t] for the i-th point
+    // of bin Own(t, fslot(c)), c = 0..8 (zero where there is none), and those points (or -1)
+    const void* fbtab;
+    const int* bjf;
+    int fbin;
+};
+
+// Extra tables of a double-word axis of length L = 16384, applied as two half-length
+// transforms (jt_axis_dw_big.cu).  Owned by the plan.
+struct BigAxisDev {
+    int n = 0, nu0 = 0, rank = 0;
+    int max_ctas = 0;             // rows of `part` (CTAs of one launch)
+    const Cx<dw>* vtab = nullptr;  // rank x L: v_k at bins nu0..n-1 (the axis table)
+    const Cx<dw>* utab = nullptr;  // rank x n: u_k (parity 0)
+    const Cx<dw>* utab1 = nullptr; // rank x n: u_k[j] e^{2 pi i m_j / L} (parity 1)
+    const dw* vblk = nullptr;      // nu0 x n dense block
+    const Cx<dw>* tw2 = nullptr;   // L/2: e^{2 pi i s / (L/2)}
+    const int* mtab2 = nullptr;    // n: m_j mod L/2
+    const int* bin_ptr2 = nullptr; // L/2 + 1: points of bin m' = m_j mod L/2
+    const int* bin_idx2 = nullptr; // n
+    dw* part = nullptr;            // max_ctas x n partial sums
 };
 
 // ------------------------------------------------------------------ clusters
@@ -408,7 +514,7 @@ __device__ __forceinline__ void stockham_pass(Cx<R>* x, R* sre, R* sim, const Cx
         for (int e = 0; e < E; ++e) {
             int b = e % NB, r = e / NB;
             int idx = t + T * b + r * (L / RX);
-            x[e] = Cx<R>{sre[S::pad(idx)], sim[S::pad(idx)]};
+            x[e] = XBuf<R>{sre, sim}.template get<S>(idx);
         }
         group_sync<T, G>(g);  // every read done before this pass writes
     }
@@ -430,11 +536,7 @@ __device__ __forceinline__ void stockham_pass(Cx<R>* x, R* sre, R* sim, const Cx
         } else {
             const int base = (j - k) * RX + k;
 #pragma unroll
-            for (int q = 0; q < RX; ++q) {
-                int idx = base + q * NS;
-                sre[S::pad(idx)] = a[q].re;
-                sim[S::pad(idx)] = a[q].im;
-            }
+            for (int q = 0; q < RX; ++q) XBuf<R>{sre, sim}.template put<S>(base + q * NS, a[q]);
         }
     }
     if constexpr (!LAST) group_sync<T, G>(g);  // writes visible to the next pass
@@ -465,6 +567,13 @@ struct Lean {
     static constexpr bool value = Shape<R, LOG2L>::THREADS >= 1024;
 };
 
+// Double-word instances up to L = 2048 read their twiddles from a per-CTA copy in shared
+// memory instead of the (L1-cached) table: every rank term of every fibre re-reads them.
+template <class R, int LOG2L>
+struct TwSmem {
+    static constexpr bool value = sizeof(R) == 8 && LOG2L >= 1 && LOG2L <= 11;
+};
+
 // CTAs of 256 threads are held to 128 registers a thread, so that two of them fit an SM.
 template <class R, int LOG2L, bool FWD, bool SPLIT = false>
 __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::THREADS <= 256) ? 2 : 1)
@@ -479,16 +588,23 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
     R* smem = reinterpret_cast<R*>(smem_raw);
     const int g = threadIdx.x / T;
     const int t = threadIdx.x % T;
-    // per group: FFT buffer (re, im) then an auxiliary buffer of L reals
-    R* sre = smem + (size_t)g * (2 * S::PADL + L);
+    // per group: FFT buffer (2 PADL reals), then an auxiliary buffer of L reals
+    R* sre = smem + (size_t)g * S::GSTRIDE;
     R* sim = sre + S::PADL;
-    R* aux = sim + S::PADL;
+    R* aux = sre + 2 * S::PADL;
+    const XBuf<R> xb{sre, sim};
 
     const int n = A.n, nu0 = A.nu0, rank = A.rank;
     const Cx<R>* __restrict__ vtab = reinterpret_cast<const Cx<R>*>(A.vtab);
     const Cx<R>* __restrict__ utab = reinterpret_cast<const Cx<R>*>(A.utab);
     const R* __restrict__ vblk = reinterpret_cast<const R*>(A.vblk);
-    const Cx<R>* __restrict__ tw = reinterpret_cast<const Cx<R>*>(A.twid);
+    const Cx<R>* tw = reinterpret_cast<const Cx<R>*>(A.twid);
+    if constexpr (TwSmem<R, LOG2L>::value) {
+        Cx<R>* tws = reinterpret_cast<Cx<R>*>(smem + (size_t)G * S::GSTRIDE);
+        for (int i = threadIdx.x; i < L; i += S::THREADS) tws[i] = tw[i];
+        __syncthreads();
+        tw = tws;
+    }
     const long long ntiles = (nfib + G - 1) / G;
     const unsigned csize = SPLIT ? cluster_size() : 1u, crank = SPLIT ? cluster_rank() : 0u;
     const int kb = (int)(((long long)rank * crank) / csize), ke = (int)(((long long)rank * (crank + 1)) / csize);
@@ -552,10 +668,7 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     int m = t + T * e;
-                    if (m <= L / 2) {
-                        sre[S::pad(m)] = x[e].re;
-                        sim[S::pad(m)] = x[e].im;
-                    }
+                    if (m <= L / 2) xb.template put<S>(m, x[e]);
                 }
                 group_sync<T, G>(g);
                 const Cx<R>* uk = utab + (size_t)k * n;
@@ -564,7 +677,7 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                     int j = t + T * e;
                     if (j < n) {
                         const int m = LEAN ? __ldg(A.mtab + j) : mj[e];
-                        Cx<R> y{sre[S::pad(m)], sim[S::pad(m)]};
+                        const Cx<R> y = xb.template get<S>(m);
                         acc[e] = acc[e] + re_mul(uk[j], y);
                     }
                 }
@@ -701,7 +814,7 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
 template <class R, int LOG2L>
 constexpr size_t axis_smem_bytes() {
     using S = Shape<R, LOG2L>;
-    return sizeof(R) * (size_t)S::G * (2 * S::PADL + S::L);
+    return sizeof(R) * (size_t)S::G * S::GSTRIDE + (TwSmem<R, LOG2L>::value ? sizeof(Cx<R>) * (size_t)S::L : 0);
 }
 
 }  // namespace dev

@@ -38,7 +38,17 @@ int auto_ksplit_f32(int log2L, bool fwd, bool strided, long long nfib, int rank)
 int auto_ksplit_dw(int log2L, bool fwd, long long nfib, int rank);
 
 constexpr int MAX_LOG2L_F32 = 14;
-constexpr int MAX_LOG2L_DW = 13;
+constexpr int MAX_LOG2L_DW = 14;
+// Double-word lengths up to 2^13 run in shared memory (jt_axis.cuh); 2^14 as two half-length
+// transforms (jt_axis_dw_big.cu).
+constexpr int DW_SMEM_MAX_LOG2L = 13;
+
+// L = 16384 double-word sweeps (two half-length transforms a rank term, partial sums in the
+// plan's buffer B.part, a fixed-order reduction into out).  in may equal out.
+cudaError_t launch_axis_dw_big(const dev::BigAxisDev& B, bool fwd, const double* in, double* out, long long nfib,
+                               long long inner, cudaStream_t s);
+cudaError_t dw_big_init();  // kernel attributes (before any capture)
+size_t dw_big_smem_bytes();
 
 // FP32 lengths 16..4096 use the four-step kernel (jt_warp.cuh), whose dense-block table rows
 // are padded with zeros to length L: vblk[c * L + j] = sqrt(w_j) P~_c(t_j) for j < n.

@@ -144,6 +144,19 @@ struct Own {
     }
 };
 
+// Forward with at most two points a bin: the outputs a lane keeps after step B are the bins
+// Own(t, fslot(c)), c = 0..8: slots 0..7 lie at or below L/2 for every lane, slot 8 only on
+// lane 0 (bin L/2).  Together they cover the bins 0..L/2 once, so each lane accumulates the
+// points of its own bins and no gather through shared memory is needed.
+template <int LOG2L>
+__host__ __device__ constexpr int fslot(int c) {
+    using S = WShape<LOG2L>;
+    if (S::T == 1) return c;
+    if (S::T <= 16) return (c < 8) ? (c / (S::T / 2)) * S::T + c % (S::T / 2) : S::T / 2;
+    if (S::T == 32) return c;
+    return (c < 8) ? (c / (S::R / 2)) * S::R + c % (S::R / 2) : S::R / 2;
+}
+
 // Sum CNT values per lane over the lanes of a group (xor offsets OFF, OFF/2, .., 1) so that
 // each lane keeps a share: at every step the lanes with that offset bit set keep the upper
 // half of their live values and add the partner's copy of it, so after log2(CNT) steps lane u
@@ -216,6 +229,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     const float2* __restrict__ tw = reinterpret_cast<const float2*>(A.twid);
     const float2* __restrict__ ubtab = reinterpret_cast<const float2*>(A.ubtab);
     const float2* __restrict__ vown = reinterpret_cast<const float2*>(A.vown);
+    const float2* __restrict__ fbtab = reinterpret_cast<const float2*>(A.fbtab);
+    bool fbin = FWD && A.fbin != 0;
 
     // step-A twiddles w_L^{t k1}, k1 = 1..15: fixed per lane (they depend on L only)
     // (T >= 64: in shared memory instead, written here and first read after the barriers
@@ -250,6 +265,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         vblk = reinterpret_cast<const float*>(A.vblk);
         ubtab = reinterpret_cast<const float2*>(A.ubtab);
         vown = reinterpret_cast<const float2*>(A.vown);
+        fbtab = reinterpret_cast<const float2*>(A.fbtab);
+        fbin = FWD && A.fbin != 0;
 #pragma unroll
         for (int i = 0; i < NPK; ++i) {
             if constexpr (FWD) {
@@ -259,7 +276,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     const int j = t + T * (2 * i + h);
                     if (j < n) v[h] = (unsigned)S::ypad(__ldg(A.mtab + j));
                 }
-                pk[i] = v[0] | (v[1] << 16);
+                pk[i] = fbin ? 0u : (v[0] | (v[1] << 16));
             } else {
                 pk[i] = (unsigned)__ldg(A.ovftab + 2 * t + i);
             }
@@ -374,7 +391,10 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             }
         }
 
-        float acc[16];
+        // forward with fbin: 18 partial sums in bin order (slot c, point i at 2c + i); otherwise
+        // 16 in natural order (point t + T e at e)
+        float acc[18];
+        acc[16] = acc[17] = 0.0f;
         __syncthreads();  // the previous tile is done with aux and the exchange region
         if constexpr (FWD) {
             // lengths L >= 1024 keep the whole fibre here instead of in registers (it is
@@ -400,7 +420,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         if (SPLIT && crank != 0) {
             // rank-split partners: the dense block belongs to the first CTA of the cluster
 #pragma unroll
-            for (int e = 0; e < 16; ++e) acc[e] = 0.0f;
+            for (int e = 0; e < 18; ++e) acc[e] = 0.0f;
         } else if constexpr (FWD) {
             // FT x L outputs, 16 per thread: JPT points x FPT fibres
             constexpr int JPT = (L > 256) ? L / 256 : 1;
@@ -428,8 +448,16 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
 #pragma unroll
                 for (int jj = 0; jj < JPT; ++jj) vres[(fb + FSTEP * ff) * L + j0 + 256 * jj] = part[ff * JPT + jj];
             __syncthreads();
+            if (fbin) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) acc[e] = vres[fl * L + t + T * e];
+                for (int q = 0; q < 18; ++q) {
+                    const int j = __ldg(A.bjf + q * T + t);
+                    acc[q] = (j >= 0) ? vres[fl * L + j] : 0.0f;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) acc[e] = vres[fl * L + t + T * e];
+            }
         } else if constexpr (FT <= 2) {
             // alpha_c(fibre) = sum_j vblk[c][j] g_j with one or two fibres a tile (L >= 2048):
             // every thread takes L/256 points of each fibre and all degrees, so that its table
@@ -714,7 +742,18 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     for (int k2 = 0; k2 < T; ++k2) y[q * T + k2] = a[k2];
                 }
             }
-            if constexpr (FWD) {
+            if (fbin) {
+                // acc at the points of the lane's own bins += Re(u_k y), u_k in bin order
+                const float2* fbk = fbtab + (size_t)k * (18 * T);
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    const Cx<float> yc = y[fslot<LOG2L>(c)];
+                    const float2 u0 = __ldg(fbk + (2 * c) * T + t);
+                    const float2 u1 = __ldg(fbk + (2 * c + 1) * T + t);
+                    acc[2 * c] = fmaf(u0.x, yc.re, fmaf(-u0.y, yc.im, acc[2 * c]));
+                    acc[2 * c + 1] = fmaf(u1.x, yc.re, fmaf(-u1.y, yc.im, acc[2 * c + 1]));
+                }
+            } else if constexpr (FWD) {
                 // Y[m] for m <= L/2 into the gather buffer, then acc_j += Re(u_k[j] Y[m_j])
                 gsync<T, FT>(fl);
 #pragma unroll
@@ -740,6 +779,20 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                     acc[o] = fmaf(v.x, y[o].re, fmaf(-v.y, y[o].im, acc[o]));
                 }
             }
+        }
+
+        if (fbin) {
+            // bin order back to natural order through the exchange region
+            float* nat = reinterpret_cast<float*>(smem_raw);
+            __syncthreads();  // every group is done with the exchange region
+#pragma unroll
+            for (int q = 0; q < 18; ++q) {
+                const int j = __ldg(A.bjf + q * T + t);
+                if (j >= 0) nat[fl * L + j] = acc[q];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[e] = nat[fl * L + t + T * e];
         }
 
         // store
