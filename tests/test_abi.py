@@ -73,7 +73,7 @@ def test_too_long_axis_is_not_supported(lib):
         B.jt_plan_create([16385], [0.0], [0.0], None, 1e-7)
     assert e.value.status == B.JT_ENOTSUP
     with pytest.raises(B.JTError) as e:
-        B.jt_plan_create([8193], [0.0], [0.0], None, 1e-12, B.options("split"))
+        B.jt_plan_create([16385], [0.0], [0.0], None, 1e-12, B.options("split"))
     assert e.value.status == B.JT_ENOTSUP
 
 

@@ -134,11 +134,14 @@ def test_2d_nonuniform_forward_adjoint(torch_dev, prec):
     assert e.value.status == B.JT_ENOTSUP
 
 
-@pytest.mark.parametrize("n", [(64, 48), (20, 24, 32), (300,)])
-def test_plain_fp64_path(torch_dev, n):
+@pytest.mark.parametrize("n,nrhs", [((64, 48), 3), ((20, 24, 32), 2), ((300,), 1030), ((40, 36), 1)])
+def test_plain_fp64_path(torch_dev, n, nrhs):
+    """The plain r^d path against the oracle.  Right-hand sides go in chunks (up to 1024 for
+    small boxes) with one d-dimensional cuFFT call per rank-term tuple; 1030 right-hand sides
+    of n = 300 take one chunk of 1024 and six single ones."""
     torch, dev = torch_dev
     ab = [(0.3, -0.4), (-0.5, 0.2), (0.1, 0.1)][: len(n)]
-    alpha = syn.normal(77, 0, n)
+    alpha = syn.normal(77, 0, (nrhs,) + n)
     T = make(n, ab, "fp64_plain")
     M = mats_for(n, ab)
     x = to_dev(torch, dev, alpha, "fp64_plain")
@@ -179,36 +182,50 @@ def test_nan_input_propagates_without_fault(torch_dev):
     assert torch.isnan(f).any()
 
 
-def test_stability_round_trip(torch_dev):
-    """|| (WJ)^T (WJ) v - v || / || v || (Eq. eq:stability) at eps = 1e-8, 1-D n = 1024,
-    a = b = 0: of order 1e-8 (the paper prints 0.69e-8)."""
+@pytest.mark.parametrize("n,printed", [((1024,), 0.69e-8), ((8192,), None), ((16384,), None), ((512, 512), 0.24e-8)])
+def test_stability_round_trip(torch_dev, n, printed):
+    """|| (WJ)^T (WJ) v - v || / || v || (Eq. eq:stability) of the split GPU operator at
+    eps = 1e-8, a = b = 0: within a factor 20 of the value Table tb:stability prints (1-D
+    log2 n = 10: 0.69e-8; 2-D log2 n = 9: 0.24e-8), and of the caption's order 1e-8 (below
+    2e-7) at the lengths the table does not print (1-D log2 n = 13 and 14)."""
     torch, dev = torch_dev
-    T = make((1024,), [(0.0, 0.0)], "split", eps=1e-8)
-    v = to_dev(torch, dev, syn.normal(12, 0, (4, 1024)), "split")
+    T = make(n, [(0.0, 0.0)] * len(n), "split", eps=1e-8)
+    v = to_dev(torch, dev, syn.normal(12 + n[0], 0, (4,) + n), "split")
     back = T.inverse(T.forward(v))
-    q = (back - v).norm(dim=1) / v.norm(dim=1)
-    assert float(q.max()) < 2e-7
+    q = (back - v).reshape(4, -1).norm(dim=1) / v.reshape(4, -1).norm(dim=1)
+    bound = 20 * printed if printed else 2e-7
+    assert float(q.max()) < bound, float(q.max())
 
 
-def test_autograd_gradient_matches_dense_transpose_and_finite_differences(torch_dev):
-    """Loss ||J alpha - y||^2 on a nonuniform 2-D grid (a = b = 0.25): the gradient through
-    the adjoint kernel equals 2 J^T (J alpha - y); central differences of a quadratic have
-    no truncation error, so a step of 1 isolates rounding."""
+@pytest.mark.parametrize("size", ["96x64", "1024x1024"])
+def test_autograd_gradient_matches_dense_transpose_and_finite_differences(torch_dev, size):
+    """Loss ||J alpha - y||^2 on a nonuniform 2-D grid (t_x, t_y i.i.d. U(0, pi), sorted;
+    a = b = 0.25): the gradient through the adjoint kernel equals the oracle's dense
+    2 J^T (J alpha - y) on every entry; central differences of a quadratic have no truncation
+    error, so a step of 1 along 8 seeded unit directions isolates rounding.  1024 x 1024 is the
+    differentiation workload itself (its points, alpha and y)."""
     torch, dev = torch_dev
     from paper_1901_07275_gb300 import jacobi_fn
 
-    n = (96, 64)
-    ab = [(0.25, 0.25), (0.25, 0.25)]
-    pts = [np.sort(np.pi * syn.uniform(1005, 2, (m,), offset=k * 100000)) for k, m in enumerate(n)]
-    alpha = syn.normal(1005, 0, n)
-    y = syn.normal(1005, 1, n)
+    if size == "1024x1024":
+        w = syn.workload("2d-nonuniform-1024")
+        n, ab, pts, alpha, y = tuple(w["n"]), w["ab"], w["points"], w["alpha"][0], w["y"][0]
+    else:
+        n = (96, 64)
+        ab = [(0.25, 0.25), (0.25, 0.25)]
+        pts = [np.sort(np.pi * syn.uniform(1005, 2, (m,), offset=k * 100000)) for k, m in enumerate(n)]
+        alpha = syn.normal(1005, 0, n)
+        y = syn.normal(1005, 1, n)
     T = make(n, ab, "fp32", points=pts)
     a_t = to_dev(torch, dev, alpha, "fp32").requires_grad_(True)
     y_t = to_dev(torch, dev, y, "fp32")
     loss = ((jacobi_fn(a_t, T) - y_t) ** 2).sum()
     loss.backward()
     M = mats_for(n, ab, pts)
-    ref = 2 * oracle.adjoint(oracle.forward(alpha, M) - y, M)
+    # the oracle sees the inputs the kernels saw (FP32-rounded alpha and y)
+    a32 = alpha.astype(np.float32).astype(np.float64)
+    y32 = y.astype(np.float32).astype(np.float64)
+    ref = 2 * oracle.adjoint(oracle.forward(a32, M) - y32, M)
     grad = a_t.grad.double().cpu().numpy()
     assert rel(grad, ref) < 1e-5
     with torch.no_grad():
@@ -238,11 +255,12 @@ def test_2d_nonuniform_1024_full(torch_dev):
 @pytest.mark.parametrize(
     "prec,n",
     [("fp32", 16384), ("split", 8192), ("fp32", 12000), ("split", 5000), ("fp32", 2048), ("fp32", 3000), ("fp32", 4096),
-     ("fp32", 1500)],
+     ("fp32", 1500), ("split", 16384), ("split", 12000), ("split", 8193)],
 )
 def test_1d_long_sampled(torch_dev, prec, n):
-    """Longest supported axes (n = 16384 FP32, 8192 split) and ragged lengths: 96 seeded
-    output rows against the oracle's rows of W J; the adjoint through <W J^T g, e_i>."""
+    """Longest supported axes (n = 16384 in FP32 and in split precision, where L = 16384 runs as
+    two half-length double-word transforms) and ragged lengths: 96 seeded output rows against
+    the oracle's rows of W J; the adjoint through <W J^T g, e_i>."""
     torch, dev = torch_dev
     ab = [(0.1, -0.3)]
     alpha = syn.normal(300 + n, 0, (2, n))
@@ -257,6 +275,35 @@ def test_1d_long_sampled(torch_dev, prec, n):
     g[0, rows] = syn.normal(302 + n, 0, (rows.size,))
     a = T.adjoint(to_dev(torch, dev, g, prec)).double().cpu().numpy()
     assert rel(a, g[:, rows] @ Q) < TOL[prec]
+
+
+@pytest.mark.parametrize("n,nrhs", [((9000, 3), 2), ((2, 10000), 1), ((12000,), 160)])
+def test_split_half_length_path(torch_dev, n, nrhs):
+    """Split precision with an axis of 8192 < n <= 16384 (two half-length double-word
+    transforms, partial sums over CTAs): a strided long axis, a contiguous one, and a batch of
+    160 right-hand sides (more fibres than one launch takes, so the sweep runs in chunks).
+    Forward on 128 sampled outputs against the oracle's rows; the adjoint by the transpose
+    identity <A x, y> = <x, A^T y> against the forward just checked."""
+    torch, dev = torch_dev
+    ab = [(0.15, -0.35), (-0.2, 0.3)][: len(n)]
+    alpha = syn.normal(7000 + n[0], 0, (nrhs,) + n)
+    T = make(n, ab, "split")
+    f = T.forward(to_dev(torch, dev, alpha, "split")).cpu().numpy()
+    S = 128
+    idx = np.stack([syn.integers(7001 + n[0], 3 + 10 * a, S, 0, n[a]) for a in range(len(n))], axis=1)
+    rr = syn.integers(7002 + n[0], 3, S, 0, nrhs)
+    rows = [oracle.uniform_rows(a, b, n[k], idx[:, k]) for k, (a, b) in enumerate(ab)]
+    ref = np.empty(S)
+    for s_ in range(S):
+        # one sampled output of right-hand side rr[s_]
+        ref[s_] = oracle.forward_sampled(alpha[rr[s_]], [r[s_:s_ + 1] for r in rows], idx[s_:s_ + 1])[0]
+    got = f[(rr,) + tuple(idx[:, a] for a in range(len(n)))]
+    assert rel(got, ref) < TOL["split"]
+    y = syn.normal(7003 + n[0], 0, (nrhs,) + n)
+    g = T.adjoint(to_dev(torch, dev, y, "split")).cpu().numpy()
+    lhs = float((f * y).sum())
+    rhs = float((g * alpha).sum())
+    assert abs(lhs - rhs) <= 1e-10 * np.linalg.norm(alpha) * np.linalg.norm(y)
 
 
 def test_2d_1024_uniform_sampled(torch_dev):

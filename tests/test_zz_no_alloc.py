@@ -7,7 +7,9 @@ library instead.  It exists for callers that must not ask for device memory whil
 a serving loop that cannot risk an allocation failure or the allocator's locks in the middle
 of a request, or a process whose free device memory is already held by another allocator.
 These tests call it through the C ABI and compare it with jt_forward on the same plan, on two
-calls in a row (the second call finds the previous call's data in the shared array).  This
+calls in a row (the second call finds the previous call's data in the shared array), up to the
+largest documented size (512 x 512, 12 MiB of the 16 MiB), and check that a call leaves the
+device's free memory unchanged.  This
 file is collected last so that a run stopping at its first failure has run everything else.
 """
 
@@ -34,7 +36,8 @@ def torch_dev():
 
 @pytest.mark.parametrize(
     "n,ab",
-    [((128, 96), [(0.3, -0.4), (-0.5, 0.2)]), ((1000,), [(-0.25, 0.5)]), ((16, 24, 20), [(0.1, 0.2)] * 3)],
+    [((128, 96), [(0.3, -0.4), (-0.5, 0.2)]), ((1000,), [(-0.25, 0.5)]), ((16, 24, 20), [(0.1, 0.2)] * 3),
+     ((512, 512), [(0.3, -0.4), (-0.5, 0.2)])],
 )
 def test_noalloc_forward_matches_jt_forward_on_two_calls(torch_dev, n, ab):
     torch, dev = torch_dev
@@ -44,11 +47,16 @@ def test_noalloc_forward_matches_jt_forward_on_two_calls(torch_dev, n, ab):
         x = torch.tensor(syn.normal(41, 0, (2,) + n), dtype=torch.float64, device=dev)
         ref = torch.empty_like(x)
         B.jt_forward(plan, x.data_ptr(), ref.data_ptr(), 2, stream)
-        for _ in range(2):
-            out = torch.full_like(x, float("nan"))
-            B.jt_forward_plain_noalloc(plan, x.data_ptr(), out.data_ptr(), 2, stream)
+        outs = [torch.full_like(x, float("nan")) for _ in range(2)]
+        torch.cuda.synchronize()
+        for i in range(2):
+            free0 = torch.cuda.mem_get_info(dev)[0]
+            B.jt_forward_plain_noalloc(plan, x.data_ptr(), outs[i].data_ptr(), 2, stream)
             torch.cuda.synchronize()
-            err = float((out - ref).norm() / ref.norm())
+            free1 = torch.cuda.mem_get_info(dev)[0]
+            # the call itself asks the device for nothing
+            assert free1 == free0, (free0, free1)
+            err = float((outs[i] - ref).norm() / ref.norm())
             assert np.isfinite(err) and err <= TOL, err
     finally:
         B.jt_destroy(plan)
@@ -58,11 +66,17 @@ def test_noalloc_rejects_plans_it_cannot_serve(torch_dev):
     torch, dev = torch_dev
     stream = torch.cuda.current_stream().cuda_stream
     big = B.jt_plan_create((1024, 1024), [0.1, 0.1], [0.2, 0.2], None, 1e-8, B.options("fp64_plain"), stream)
+    # just past a power of two: each FFT length doubles, so the work space passes 16 MiB
+    odd = B.jt_plan_create((513, 513), [0.1, 0.1], [0.2, 0.2], None, 1e-8, B.options("fp64_plain"), stream)
     fp32 = B.jt_plan_create((64,), [0.1], [0.2], None, 1e-7, B.options("fp32"), stream)
     try:
         x = torch.zeros((1024, 1024), dtype=torch.float64, device=dev)
         with pytest.raises(B.JTError) as e:
             B.jt_forward_plain_noalloc(big, x.data_ptr(), x.data_ptr(), 1, stream)
+        assert e.value.status == B.JT_EINVAL
+        z = torch.zeros((513, 513), dtype=torch.float64, device=dev)
+        with pytest.raises(B.JTError) as e:
+            B.jt_forward_plain_noalloc(odd, z.data_ptr(), z.data_ptr(), 1, stream)
         assert e.value.status == B.JT_EINVAL
         y = torch.zeros(64, dtype=torch.float64, device=dev)
         with pytest.raises(B.JTError) as e:
@@ -70,4 +84,5 @@ def test_noalloc_rejects_plans_it_cannot_serve(torch_dev):
         assert e.value.status == B.JT_ENOTSUP
     finally:
         B.jt_destroy(big)
+        B.jt_destroy(odd)
         B.jt_destroy(fp32)
