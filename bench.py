@@ -36,8 +36,8 @@ N = (512, 512)
 AB = [(0.3, -0.4), (-0.5, 0.2)]
 METRIC = "Jacobi coeffs/sec (2-D 512x512 forward+inverse, FP32 fused axis kernels, rel l2 <= 1e-5 vs FP64 oracle)"
 UNIT = "coeffs/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128  # used only for the nominal figure beside the measured peak
+SPLIT_MAX_N = 16384  # longest axis of a split (double-word) plan
 
 
 def load_peaks():
@@ -69,6 +69,13 @@ def captured_traffic():
         return None
 
 
+# FP32 flops of the double-word arithmetic per real flop of the algorithmic count: a sum is
+# SloppyDWPlusDW (11 FP32 operations), a product the FMA-based DWTimesDW (9 operations, 3 of them
+# FMAs: 12 flops); the FFT count 5 L log2 L is 60 % sums and 40 % products (a radix-2 butterfly:
+# 6 sums, 4 products), so one real flop costs 0.6 x 11 + 0.4 x 12 = 11.4 FP32 flops.
+DW_FLOPS_PER_FLOP = 0.6 * 11 + 0.4 * 12
+
+
 def axis_flops(n, L, r):
     """Algorithmic FP32 flops of one fibre of one axis: r (5 L log2 L + 8 n) + 55 n."""
     return r * (5 * L * math.log2(L) + 8 * n) + 55 * n
@@ -81,7 +88,7 @@ def axis_table_bytes(n, L, r, nu0, real_bytes):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -97,7 +104,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -245,6 +252,38 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- GPU arm
+def fp32_peak(dev, stream, gpu_index):
+    """The FP32 rate that bounds the axis kernels, measured: jt_probe_fp32_fma (independent FMA
+    chains over 4 CTAs of 256 threads per SM) as one FMA an instruction and as two
+    (fma.rn.f32x2), each launch about 50 ms, timed with CUDA events on the launching stream
+    with the clocks sampled during it; the best of 3 launches per form."""
+    import torch
+
+    from paper_1901_07275_gb300 import binding as B
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(1024 * sms, dtype=torch.float32, device=dev)
+    out = {"sm_count": sms}
+    iters = 100000
+    for label, paired in (("fma_f32", False), ("fma_f32x2", True)):
+        B.jt_probe_fp32_fma(paired, 1000, sink.data_ptr(), sink.numel(), stream.cuda_stream)  # warm-up
+        torch.cuda.synchronize()
+        best = None
+        with ClockSampler(gpu_index) as clk:
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                flops = B.jt_probe_fp32_fma(paired, iters, sink.data_ptr(), sink.numel(), stream.cuda_stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tf = flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+                best = tf if best is None else max(best, tf)
+        c = clk.summary()
+        out[label] = {"tflops": best, "sm_mhz": c["sm_mhz"], "clock_samples": c["samples"], "reasons": c["reasons"]}
+    out["peak_tflops"] = max(out["fma_f32"]["tflops"], out["fma_f32x2"]["tflops"])
+    return out
+
+
 def other_configs(dev, stream):
     """Throughput of the FP32 kernels on the other workloads (forward + inverse/adjoint per
     step, CUDA events, 2 warm-up and 3 timed steps each)."""
@@ -489,21 +528,26 @@ def batch_mix_throughput(dev, stream, count=64):
 def batch_full_mix(dev, stream, count=512):
     """The whole serving mix: 512 members (a fair coin between 1-D n log-uniform in
     [256, 16384] and 2-D n_x, n_y log-uniform in [64, 1024]; (a, b) ~ U(-0.5, 0.5) per axis;
-    1..16 right-hand sides).  FP32 at eps 1e-7: plans by create_many (host setups side by side),
-    the rank split of every member's sweeps measured for its nrhs (jt_plan_tune), then one
-    batched forward + adjoint per step, eager and replayed from a CUDA graph.  Double-word
-    (split, eps 1e-12): the same for the first 64 members whose axes the split kernels take
-    (n <= 8192).  The coefficients are seeded normals drawn on the device (torch generator,
-    seed 1004 + member): at 286 M coefficients the host generator would dominate the run."""
+    1..16 right-hand sides).  FP32 at eps 1e-7 and double-word (split) at eps 1e-12: plans by
+    create_many (host setups side by side), the rank split of every member's sweeps measured
+    for its nrhs (jt_plan_tune), then one batched forward + adjoint per step, eager and replayed
+    from a CUDA graph.  The coefficients of member i are the seeded host normals
+    synthetic.normal(5000 + i, 0, .) -- the inputs on which tests/test_gpu_batch_mix.py checks
+    every member against the oracle."""
     import torch
 
     from paper_1901_07275_gb300 import Batch, Transform
     from paper_1901_07275_gb300 import synthetic as syn
 
     mix = syn.batch_mix(count)
-    out = {"members": count, "one_d_members": sum(len(m["n"]) == 1 for m in mix)}
-    for prec, eps, members in (("fp32", 1e-7, mix),
-                               ("split", 1e-12, [m for m in mix if max(m["n"]) <= 8192][:64])):
+    out = {"members": count, "one_d_members": sum(len(m["n"]) == 1 for m in mix),
+           "inputs": "seeded host generator, synthetic.normal(5000 + member, 0, (nrhs,) + n)"}
+    t0 = time.perf_counter()
+    host = [syn.normal(5000 + i, 0, (m["nrhs"],) + tuple(m["n"])) for i, m in enumerate(mix)]
+    out["input_generation_s"] = time.perf_counter() - t0
+    split_idx = [i for i, m in enumerate(mix) if max(m["n"]) <= SPLIT_MAX_N]
+    for prec, eps, idx in (("fp32", 1e-7, list(range(count))), ("split", 1e-12, split_idx)):
+        members = [mix[i] for i in idx]
         t0 = time.perf_counter()
         Ts = Transform.create_many([{"n": m["n"], "a": [p[0] for p in m["ab"]], "b": [p[1] for p in m["ab"]],
                                      "eps": eps, "precision": prec} for m in members])
@@ -514,11 +558,7 @@ def batch_full_mix(dev, stream, count=512):
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t0
         dt = torch.float32 if prec == "fp32" else torch.float64
-        gen = torch.Generator(device=dev)
-        xs = []
-        for i, m in enumerate(members):
-            gen.manual_seed(1004 + i)
-            xs.append(torch.randn((m["nrhs"],) + tuple(m["n"]), generator=gen, device=dev, dtype=dt))
+        xs = [torch.tensor(host[i], dtype=dt, device=dev) for i in idx]
         fs = [torch.empty_like(x) for x in xs]
         gs = [torch.empty_like(x) for x in xs]
         t0 = time.perf_counter()
@@ -644,7 +684,10 @@ def main():
     bytes_step = 2 * sum(2 * 4 * nrhs * N[0] * N[1] + axis_table_bytes(N[a], Ls[a], ranks[a], 27, 4) for a in range(2))
     achieved_tflops = flops_step * args.steps / (kern_ms * 1e-3) / 1e12
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    nominal_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    probe = fp32_peak(dev, stream, gpu_index)
+    alu_peak = probe["peak_tflops"]
     hbm_gbs = bytes_step * args.steps / (kern_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     launches = 4 * args.steps
@@ -662,8 +705,12 @@ def main():
                      "frac": achieved_tflops / alu_peak, "traffic": captured_traffic(),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "algorithmic_bytes_per_launch": bytes_step / 4,
-                     "peak_note": f"FP32 CUDA-core peak {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                                  f"{sm_max:.0f} MHz (sm_max from MEASURED_PEAKS: {peak_src})",
+                     "peak_note": "measured: best FP32 FMA-chain rate of jt_probe_fp32_fma (scalar and "
+                                  "f32x2 forms) in this run",
+                     "peak_probe": probe,
+                     "nominal_peak": {"tflops": nominal_peak,
+                                      "rule": f"{sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
+                                              f"(sm_max from MEASURED_PEAKS: {peak_src})"},
                      "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
                              "peak_source": peak_src}},
         "clocks": clocks, "gpu_launches": launches,
@@ -745,14 +792,26 @@ def main():
         err2 = float(np.linalg.norm(f2[:1].cpu().numpy() - ref2) / np.linalg.norm(ref2))
         err2i = float(np.linalg.norm(y2[:1].cpu().numpy() - alpha[:1]) / np.linalg.norm(alpha[:1]))
         split_v = 2 * n2 * N[0] * N[1] / (split_ms * 1e-3)
-        line["split"] = {"value": split_v, "unit": UNIT, "nrhs": n2, "ms_per_step": split_ms, "ranks": T2.ranks,
+        # roofline of the double-word sweeps: the algorithmic count in FP32 instructions of the
+        # double-word algorithms (DW_FLOPS_PER_FLOP a real operation), over the measured FP32 peak
+        flops_split = 2 * sum(n2 * (N[0] * N[1] // N[a]) * axis_flops(N[a], T2.fft_lens[a], T2.ranks[a]) for a in range(2))
+        dw_tflops = flops_split * DW_FLOPS_PER_FLOP / (split_ms * 1e-3) / 1e12
+        line["split"] = {"roofline": {"bound": "alu", "achieved": dw_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                                      "frac": dw_tflops / alu_peak,
+                                      "algorithmic_flops_per_step": flops_split,
+                                      "dw_flops_per_flop": DW_FLOPS_PER_FLOP,
+                                      "note": "algorithmic flops x the FP32 operations of the double-word "
+                                              "algorithms (sum 11, product 12 counting an FMA as 2), timed over "
+                                              "the whole step (4 sweeps)"},
+                         "value": split_v, "unit": UNIT, "nrhs": n2, "ms_per_step": split_ms, "ranks": T2.ranks,
                          "rel_err_forward": err2, "rel_err_inverse_of_forward": err2i, "dtype": "f32x2 (f64 io)"}
         del x2, f2, y2
         T2.close()
 
-        # plain FP64 r^2-FFT path (cuFFT Z2Z), one right-hand side
+        # plain FP64 r^2-FFT path (cuFFT Z2Z): the same 64 right-hand sides as the split kernels,
+        # in chunks with one batched 2-D cuFFT call per (pattern, rank-term pair)
         Tp = Transform(N, [p[0] for p in AB], [p[1] for p in AB], eps=1e-12, precision="fp64_plain")
-        xp = torch.tensor(alpha[:1], dtype=torch.float64, device=dev)
+        xp = torch.tensor(alpha[:n2], dtype=torch.float64, device=dev)
         fp_ = torch.empty_like(xp)
         yp = torch.empty_like(xp)
         Tp.forward(xp, out=fp_)
@@ -766,9 +825,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         plain_ms = e0.elapsed_time(e1) / kp
-        errp = float(np.linalg.norm(fp_.cpu().numpy() - ref) / np.linalg.norm(ref))
-        plain_v = 2 * N[0] * N[1] / (plain_ms * 1e-3)
-        line["plain_fp64"] = {"value": plain_v, "unit": UNIT, "nrhs": 1, "ms_per_step": plain_ms,
+        errp = float(np.linalg.norm(fp_[:1].cpu().numpy() - ref) / np.linalg.norm(ref))
+        plain_v = 2 * n2 * N[0] * N[1] / (plain_ms * 1e-3)
+        line["plain_fp64"] = {"value": plain_v, "unit": UNIT, "nrhs": n2, "ms_per_step": plain_ms,
                               "ranks": Tp.ranks, "rel_err_forward": errp,
                               "speedup_fp32_over_plain": value / world / plain_v,
                               "speedup_split_over_plain": split_v / plain_v}
