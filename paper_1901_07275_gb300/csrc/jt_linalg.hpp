@@ -9,6 +9,7 @@
 #include <cmath>
 #include <complex>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 namespace jt {
@@ -18,7 +19,9 @@ using cd = std::complex<double>;
 
 // Column indices chosen, in order, by the first k steps of Householder QR with column
 // pivoting (Businger--Golub) of the m x n matrix A.  A is taken by value (a work copy).
-inline std::vector<int> qrcp_pivots(std::vector<cd> A, int m, int n, int k) {
+// The reflection of the trailing columns at each step is split over `threads` host threads
+// (the result does not depend on the split: each column is updated by one thread).
+inline std::vector<int> qrcp_pivots(std::vector<cd> A, int m, int n, int k, int threads = 1) {
     std::vector<int> perm(n);
     std::iota(perm.begin(), perm.end(), 0);
     std::vector<double> norms(n, 0.0);
@@ -52,17 +55,29 @@ inline std::vector<int> qrcp_pivots(std::vector<cd> A, int m, int n, int k) {
             vn += std::norm(v[i]);
         }
         if (vn == 0.0) continue;
-        for (int j = s + 1; j < n; ++j) {
-            cd* col = &A[(size_t)j * m];
-            cd w = 0;
-            for (int i = s; i < m; ++i) w += std::conj(v[i]) * col[i];
-            w *= 2.0 / vn;
-            double nn = 0;
-            for (int i = s; i < m; ++i) {
-                col[i] -= w * v[i];
-                if (i > s) nn += std::norm(col[i]);
+        auto update = [&](int j0, int j1) {
+            for (int j = j0; j < j1; ++j) {
+                cd* col = &A[(size_t)j * m];
+                cd w = 0;
+                for (int i = s; i < m; ++i) w += std::conj(v[i]) * col[i];
+                w *= 2.0 / vn;
+                double nn = 0;
+                for (int i = s; i < m; ++i) {
+                    col[i] -= w * v[i];
+                    if (i > s) nn += std::norm(col[i]);
+                }
+                norms[j] = nn;
             }
-            norms[j] = nn;
+        };
+        const int rest = n - (s + 1);
+        const int nt = std::max(1, std::min(threads, rest / 512));
+        if (nt <= 1) {
+            update(s + 1, n);
+        } else {
+            std::vector<std::thread> th;
+            for (int w = 0; w < nt; ++w)
+                th.emplace_back(update, s + 1 + (int)((long long)rest * w / nt), s + 1 + (int)((long long)rest * (w + 1) / nt));
+            for (auto& t : th) t.join();
         }
     }
     perm.resize(k);
