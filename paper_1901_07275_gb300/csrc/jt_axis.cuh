@@ -358,6 +358,13 @@ struct Shape {
     static constexpr int GSTRIDE = ((2 * PADL + L) + 1) & ~1;
 };
 
+// Double-word instances up to L = 2048 read their twiddles from a per-CTA copy in shared
+// memory instead of the (L1-cached) table: every rank term of every fibre re-reads them.
+template <class R, int LOG2L>
+struct TwSmem {
+    static constexpr bool value = sizeof(R) == 8 && LOG2L >= 1 && LOG2L <= 11;
+};
+
 // The exchange buffer of one group: (re, im) arrays for FP32, interleaved complex double-words.
 template <class R>
 struct XBuf {
@@ -527,7 +534,12 @@ __device__ __forceinline__ void stockham_pass(Cx<R>* x, R* sre, R* sim, const Cx
         const int k = j & (NS - 1);
         if constexpr (NS > 1) {
 #pragma unroll
-            for (int r = 1; r < RX; ++r) a[r] = cmul(a[r], tw[(r * k) * (L / (NS * RX))]);
+            for (int r = 1; r < RX; ++r) {
+                if constexpr (TwSmem<R, LOG2L>::value)  // per-pass table: [NS - R0 + (r - 1) NS + k]
+                    a[r] = cmul(a[r], tw[(NS - S::R0) + (r - 1) * NS + k]);
+                else
+                    a[r] = cmul(a[r], tw[(r * k) * (L / (NS * RX))]);
+            }
         }
         dft<RX, R>(a);
         if constexpr (LAST) {
@@ -567,13 +579,6 @@ struct Lean {
     static constexpr bool value = Shape<R, LOG2L>::THREADS >= 1024;
 };
 
-// Double-word instances up to L = 2048 read their twiddles from a per-CTA copy in shared
-// memory instead of the (L1-cached) table: every rank term of every fibre re-reads them.
-template <class R, int LOG2L>
-struct TwSmem {
-    static constexpr bool value = sizeof(R) == 8 && LOG2L >= 1 && LOG2L <= 11;
-};
-
 // CTAs of 256 threads are held to 128 registers a thread, so that two of them fit an SM.
 template <class R, int LOG2L, bool FWD, bool SPLIT = false>
 __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::THREADS <= 256) ? 2 : 1)
@@ -600,8 +605,15 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
     const R* __restrict__ vblk = reinterpret_cast<const R*>(A.vblk);
     const Cx<R>* tw = reinterpret_cast<const Cx<R>*>(A.twid);
     if constexpr (TwSmem<R, LOG2L>::value) {
+        // per pass of span NS (NS = R0, 8 R0, .. < L, radix 8 after the first pass) the twiddles
+        // w_L^{r k L / (8 NS)}, r = 1..7, k < NS, at [NS - R0 + (r - 1) NS + k]: the lanes of a
+        // pass read consecutive k, so the reads of a quarter-warp hit different banks
         Cx<R>* tws = reinterpret_cast<Cx<R>*>(smem + (size_t)G * S::GSTRIDE);
-        for (int i = threadIdx.x; i < L; i += S::THREADS) tws[i] = tw[i];
+        for (int ns = S::R0; ns < L; ns *= S::EMAX)
+            for (int i = threadIdx.x; i < (S::EMAX - 1) * ns; i += S::THREADS) {
+                const int r = 1 + i / ns, k = i % ns;
+                tws[ns - S::R0 + i] = tw[((r * k) * (L / (ns * S::EMAX))) & (L - 1)];
+            }
         __syncthreads();
         tw = tws;
     }
