@@ -445,6 +445,91 @@ def setup_timings():
     return out
 
 
+def sweep_times(dev, stream):
+    """Per-sweep times of the bench workload: the 2-D forward and adjoint, and the same 1-D
+    plan as the 2-D plan's contiguous axis over all 512 x nrhs fibres; the strided sweep is the
+    difference.  FP32 with 256 right-hand sides, split with 64."""
+    import torch
+
+    from paper_1901_07275_gb300 import Transform
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    for prec, nr, eps in (("fp32", 256, 1e-7), ("split", 64, 1e-12)):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        T2 = Transform(N, [p[0] for p in AB], [p[1] for p in AB], eps=eps, precision=prec)
+        T1 = Transform((N[1],), [AB[1][0]], [AB[1][1]], eps=eps, precision=prec)
+        x = torch.randn((nr,) + N, device=dev, dtype=dt)
+        y = torch.empty_like(x)
+        x1, y1 = x.reshape(-1, N[1]), y.reshape(-1, N[1])
+        r = {"nrhs": nr, "ranks": T2.ranks}
+        r["forward_2d_ms"] = timed(lambda: T2.forward(x, out=y))
+        r["adjoint_2d_ms"] = timed(lambda: T2.adjoint(x, out=y))
+        r["forward_contiguous_ms"] = timed(lambda: T1.forward(x1, out=y1))
+        r["adjoint_contiguous_ms"] = timed(lambda: T1.adjoint(x1, out=y1))
+        r["forward_strided_ms"] = r["forward_2d_ms"] - r["forward_contiguous_ms"]
+        r["adjoint_strided_ms"] = r["adjoint_2d_ms"] - r["adjoint_contiguous_ms"]
+        out[prec] = r
+        T1.close()
+        T2.close()
+        del x, y
+    return out
+
+
+def fac_and_app(dev, stream):
+    """Factorisation (plan creation: host setup, or its O(n^2) steps on the GPU, then the
+    upload) beside application (one forward of one right-hand side, CUDA events) for the
+    workloads, as the paper reports fac and app times side by side (Sec. 4)."""
+    import torch
+
+    from paper_1901_07275_gb300 import Transform
+    from paper_1901_07275_gb300 import synthetic as syn
+
+    out = {}
+    cases = [("1d-1024", "fp32", 1e-7), ("1d-1024", "split", 1e-12), ("2d-512", "fp32", 1e-7),
+             ("2d-512", "split", 1e-12), ("3d-256", "fp32", 1e-7), ("2d-nonuniform-1024", "fp32", 1e-7)]
+    for name, prec, eps in cases:
+        w = syn.workload(name, nrhs=1)
+        row = {"eps": eps}
+        for dev_setup in (False, True):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            T = Transform(w["n"], [p[0] for p in w["ab"]], [p[1] for p in w["ab"]], points=w["points"], eps=eps,
+                          precision=prec, setup_device=dev_setup)
+            torch.cuda.synchronize()
+            row["fac_gpu_setup_s" if dev_setup else "fac_host_s"] = time.perf_counter() - t0
+            if not dev_setup:
+                dt = torch.float32 if prec == "fp32" else torch.float64
+                x = torch.tensor(w["alpha"], dtype=dt, device=dev)
+                f = torch.empty_like(x)
+                for _ in range(3):
+                    T.forward(x, out=f)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(10):
+                    T.forward(x, out=f)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row["app_forward_ms"] = e0.elapsed_time(e1) / 10
+                row["ranks"] = T.ranks
+                del x, f
+            T.close()
+        out[f"{name} {prec}"] = row
+    return out
+
+
 def batch_mix_throughput(dev, stream, count=64):
     """The serving-style mix (1-D n log-uniform in [256, 16384] or 2-D n_x, n_y in [64, 1024],
     (a, b) ~ U(-0.5, 0.5), 1..16 right-hand sides), FP32: one batched forward + adjoint per
@@ -861,6 +946,8 @@ def main():
         line["batch"] = batch_mix_throughput(dev, stream)
         line["batch_512"] = batch_full_mix(dev, stream)
         line["setup"] = setup_timings()
+        line["fac_app"] = fac_and_app(dev, stream)
+        line["sweeps"] = sweep_times(dev, stream)
 
         if world == 1:
             line["cpu_baseline"] = oracle_throughput(nrhs)
