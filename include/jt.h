@@ -56,7 +56,7 @@ typedef enum {
     JT_ENOMEM = 2,   /* host or device allocation failed */
     JT_ENOTSUP = 3,  /* operation not defined for this plan (nonuniform inverse, ...) */
     JT_ECUDA = 4,    /* a CUDA runtime or library call failed */
-    JT_ETIMEOUT = 5, /* reserved: a bounded device wait expired */
+    JT_ETIMEOUT = 5, /* a bounded device wait expired (jt_plan_check) */
     JT_ENOCONV = 6   /* setup did not converge: rank needed for eps exceeds rank_cap, nodes not found */
 } jt_status;
 
@@ -181,6 +181,20 @@ jt_status jt_transform_host(jt_plan* plan, int direction, const void* in_host, v
  * n[0..d-1] (n[d..2] set to 1), the precision, the kind, and whether every axis uses the
  * Gauss--Jacobi nodes (so that jt_inverse is defined for the first kind). */
 jt_status jt_plan_shape(const jt_plan* plan, int* d, int64_t* n, int* prec, int* kind, int* all_uniform);
+
+/* Failure detection (no counterpart in the paper).  The FP32 forward sweeps of length up to
+ * 512 (not batched, no rank split) wait on bulk copies of their rank tables; every such wait
+ * is bounded (about one second), and a
+ * kernel whose wait runs out sets a status word of the plan and returns early, leaving its
+ * output incomplete instead of hanging.  jt_plan_check synchronises `stream`, then returns
+ * JT_ETIMEOUT (and clears the words) if any wait of this plan ran out since the last check,
+ * else JT_OK.  JT_EINVAL for a NULL plan, JT_ECUDA if the stream reports an error. */
+jt_status jt_plan_check(jt_plan* plan, jt_stream_t stream);
+
+/* Testing hook: with on != 0 the plan's FP32 forward sweeps that stream their tables issue no copy,
+ * so their first wait runs out (after about one second) and jt_plan_check reports
+ * JT_ETIMEOUT.  on = 0 restores normal operation.  JT_ENOTSUP for other precisions. */
+jt_status jt_plan_inject_wait_timeout(jt_plan* plan, int on);
 
 /* Release a plan and its device tables.  NULL is accepted. */
 void jt_destroy(jt_plan* plan);

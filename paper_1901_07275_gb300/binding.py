@@ -31,6 +31,8 @@ EXPORTS = (
     "jt_forward_plain_noalloc",
     "jt_plan_info",
     "jt_destroy",
+    "jt_plan_check",
+    "jt_plan_inject_wait_timeout",
     "jt_plan_shape",
     "jt_transform_host",
     "jt_plan_create_many",
@@ -111,6 +113,10 @@ def lib() -> ctypes.CDLL:
     L.jt_plan_info.restype = i32
     L.jt_destroy.argtypes = [vp]
     L.jt_destroy.restype = None
+    L.jt_plan_check.argtypes = [vp, vp]
+    L.jt_plan_check.restype = i32
+    L.jt_plan_inject_wait_timeout.argtypes = [vp, i32]
+    L.jt_plan_inject_wait_timeout.restype = i32
     L.jt_plan_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.jt_plan_shape.restype = i32
@@ -251,6 +257,19 @@ def jt_plan_info(plan: int, axis: int, n: int | None = None):
 
 def jt_destroy(plan: int) -> None:
     lib().jt_destroy(_ptr(plan))
+
+
+def jt_plan_check(plan: int, stream: int = 0) -> int:
+    """Synchronise `stream` and return the plan's status (JT_OK or JT_ETIMEOUT); raises on
+    other errors."""
+    st = lib().jt_plan_check(ctypes.c_void_p(plan), ctypes.c_void_p(stream))
+    if st not in (JT_OK, JT_ETIMEOUT):
+        _check(st, "jt_plan_check")
+    return st
+
+
+def jt_plan_inject_wait_timeout(plan: int, on: bool) -> None:
+    _check(lib().jt_plan_inject_wait_timeout(ctypes.c_void_p(plan), 1 if on else 0), "jt_plan_inject_wait_timeout")
 
 
 def jt_plan_shape(plan: int):

@@ -277,6 +277,11 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     if ((st = upload(ax, bjf, &p, s)) != JT_OK) return st;
     A.bjf = (const int*)p;
     A.fbin = fbin;
+    // status word of the bounded waits (cleared by jt_plan_check)
+    const std::vector<unsigned> status0(1, 0u);
+    if ((st = upload(ax, status0, &p, s)) != JT_OK) return st;
+    A.status = (unsigned*)p;
+    A.skip_copy = 0;
     // Double-word axes of length 2^14: the tables of the two half-length transforms
     // (jt_axis_dw_big.cu): u_k e^{2 pi i m_j / L}, bins m_j mod L/2 and their CSR, the
     // half-length twiddles, and the partial-sum buffer of one launch.
@@ -1066,6 +1071,30 @@ jt_status jt_forward_plain_noalloc(jt_plan* plan, const void* alpha, void* f, in
     if (plan->prec != JT_FP64_PLAIN) return JT_ENOTSUP;
     if (plan_elements(plan, nrhs) < 1) return JT_EINVAL;
     return jt::plain_apply_static(plan->plain, (const double*)alpha, (double*)f, nrhs, true, (cudaStream_t)stream);
+}
+
+jt_status jt_plan_check(jt_plan* plan, jt_stream_t stream) {
+    if (!plan) return JT_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return JT_ECUDA;
+    bool timed_out = false;
+    for (auto& ax : plan->axes) {
+        if (!ax.dev.status) continue;
+        unsigned w = 0;
+        if (cudaMemcpy(&w, ax.dev.status, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return JT_ECUDA;
+        if (w) {
+            timed_out = true;
+            const unsigned zero = 0;
+            if (cudaMemcpy(ax.dev.status, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return JT_ECUDA;
+        }
+    }
+    return timed_out ? JT_ETIMEOUT : JT_OK;
+}
+
+jt_status jt_plan_inject_wait_timeout(jt_plan* plan, int on) {
+    if (!plan) return JT_EINVAL;
+    if (plan->prec != JT_FP32) return JT_ENOTSUP;
+    for (auto& ax : plan->axes) ax.dev.skip_copy = on ? 1 : 0;
+    return JT_OK;
 }
 
 jt_status jt_plan_info(const jt_plan* plan, int axis, int* rank, int64_t* fft_len, double* t_out, double* w_out) {

@@ -426,6 +426,11 @@ struct AxisDev {
     const void* fbtab;
     const int* bjf;
     int fbin;
+    // Plan-owned status word: bit 0 is set when a bounded wait of a kernel ran out (the kernel
+    // then returns early; the plan reports JT_ETIMEOUT).  skip_copy (tests only): the FP32
+    // four-step kernel issues no table copy, so its first wait runs out.
+    unsigned* status;
+    int skip_copy;
 };
 
 // Extra tables of a double-word axis of length L = 16384, applied as two half-length

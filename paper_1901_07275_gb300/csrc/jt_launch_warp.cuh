@@ -17,7 +17,7 @@ template <int LOG2L, bool FWD, bool STRIDED, bool SPLIT>
 cudaError_t warp_launch_one(const dev::AxisDev& A, const float* in, float* out, long long nfib, long long inner,
                             int ksplit, cudaStream_t s) {
     using S = dev::WShape<LOG2L>;
-    constexpr size_t smem = dev::warp_smem_bytes<LOG2L>(STRIDED);
+    constexpr size_t smem = dev::warp_smem_bytes<LOG2L>(STRIDED, dev::WStream<LOG2L, FWD, false, SPLIT>::value);
     static const dev::BatchPtrs no_ptrs{};
     const dev::BatchJob* no_jobs = nullptr;
     const long long ntiles = (nfib + S::FT - 1) / S::FT;
@@ -81,19 +81,19 @@ int warp_auto_ksplit(int log2L, bool fwd, bool strided, long long nfib, int rank
         if (fwd && strided) {
             ki = &warp_info<LOG2L, true, true, false, false>();
             e = kern_init(*ki, dev::warp_axis_kernel<LOG2L, true, true, false, false>, S::THREADS,
-                          dev::warp_smem_bytes<LOG2L>(true), false);
+                          dev::warp_smem_bytes<LOG2L>(true, dev::WStream<LOG2L, true, false, false>::value), false);
         } else if (fwd) {
             ki = &warp_info<LOG2L, true, false, false, false>();
             e = kern_init(*ki, dev::warp_axis_kernel<LOG2L, true, false, false, false>, S::THREADS,
-                          dev::warp_smem_bytes<LOG2L>(false), false);
+                          dev::warp_smem_bytes<LOG2L>(false, dev::WStream<LOG2L, true, false, false>::value), false);
         } else if (strided) {
             ki = &warp_info<LOG2L, false, true, false, false>();
             e = kern_init(*ki, dev::warp_axis_kernel<LOG2L, false, true, false, false>, S::THREADS,
-                          dev::warp_smem_bytes<LOG2L>(true), false);
+                          dev::warp_smem_bytes<LOG2L>(true, dev::WStream<LOG2L, false, false, false>::value), false);
         } else {
             ki = &warp_info<LOG2L, false, false, false, false>();
             e = kern_init(*ki, dev::warp_axis_kernel<LOG2L, false, false, false, false>, S::THREADS,
-                          dev::warp_smem_bytes<LOG2L>(false), false);
+                          dev::warp_smem_bytes<LOG2L>(false, dev::WStream<LOG2L, false, false, false>::value), false);
         }
         if (e != cudaSuccess) return 1;
         return auto_ksplit(*ki, ntiles, rank);

@@ -102,11 +102,24 @@ constexpr int warp_nstage() {
 // Layout: exchange buffers [FT][BUF] float2, step-A twiddles [TWS] float2, fibre copies
 // [FT][AUX] float, staging buffers [NSTAGE][FT][TROW] float.
 template <int LOG2L>
-constexpr size_t warp_smem_bytes(bool strided) {
+constexpr size_t warp_smem_bytes(bool strided, bool stream = false) {
     using S = WShape<LOG2L>;
     const int ns = strided ? warp_nstage<LOG2L, true>() : 0;
-    return (size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)S::TWS * 8 + (size_t)ns * S::FT * S::TROW * 4;
+    const size_t base = (size_t)S::FT * (S::BUF * 8 + S::AUX * 4) + (size_t)S::TWS * 8 + (size_t)ns * S::FT * S::TROW * 4;
+    // streamed rank tables: two slices of 34 T float2 (16-byte aligned) and two mbarriers
+    return stream ? ((base + 15) & ~(size_t)15) + 2 * (size_t)34 * S::T * 8 + 16 : base;
 }
+
+// Single (not batched, not rank-split) forward sweeps of length up to 512 stream the rank
+// tables of each term, v_k (L) and the bin-ordered u_k (18 T), into shared memory with bulk
+// copies, one term ahead, instead of reading them through L1 right before use.  (The adjoint
+// path can stream its bin-ordered u_k and lane-ordered v_k the same way, but the extra
+// pointers spilled it and it measured slower, so it keeps the L1 loads.)
+template <int LOG2L, bool FWD, bool BATCHED, bool SPLIT>
+struct WStream {
+    static constexpr bool value = FWD && !BATCHED && !SPLIT && LOG2L <= 9;
+    static constexpr int SL = 34 * WShape<LOG2L>::T;  // float2 a slice
+};
 
 // Asynchronous 4-byte global -> shared copy (zero-filled when !valid; src must still be a
 // mapped address), and the group commit / wait of the issuing thread.
@@ -115,6 +128,45 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Bulk (TMA) copies of contiguous table slices into shared memory, completed on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// arrive once, announcing `bytes` of copies that complete on this barrier
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of `bar` with the given parity to complete, for at most about one second;
+// false if the wait ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it == 0) t0 = global_ns();
+        else if ((it & 63) == 0 && (global_ns() - t0 > 1000000000ull || it > (1u << 24))) return false;
+    }
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ float2 f2(Cx<float> c) { return make_float2(c.re, c.im); }
@@ -217,6 +269,16 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     float* aux = aux0 + (size_t)fl * S::AUX;
     // two staging buffers of FT x TROW floats (input of this tile and of the next one)
     float* stage = aux0 + (size_t)FT * S::AUX;
+    // streamed rank-table slices [2][SL] and their two mbarriers (WStream instances)
+    constexpr bool STREAM = WStream<LOG2L, FWD, BATCHED, SPLIT>::value;
+    constexpr int SL = WStream<LOG2L, FWD, BATCHED, SPLIT>::SL;
+    float2* tstream = nullptr;
+    unsigned long long* tbar = nullptr;
+    if constexpr (STREAM) {
+        const size_t off = (warp_smem_bytes<LOG2L>(STRIDED, false) + 15) & ~(size_t)15;
+        tstream = reinterpret_cast<float2*>(smem_raw + off);
+        tbar = reinterpret_cast<unsigned long long*>(tstream + 2 * SL);
+    }
 
     if constexpr (BATCHED) {
         if (njobs <= 0) return;
@@ -343,6 +405,44 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
         }
         cp_async_commit();
     };
+
+    // rank terms of this CTA (a rank-split cluster gives each CTA its share); batched launches
+    // recompute them per job in the tile loop
+    int kb = (int)(((long long)rank * crank) / csize);
+    int ke = (int)(((long long)rank * (crank + 1)) / csize);
+    // Streamed tables: slice i (the i-th term this CTA applies, over all its tiles) goes to
+    // buffer i & 1 and completes the ((i >> 1) + 1)-th phase of that buffer's mbarrier.
+    unsigned long long nslices = 0, slice = 0;
+    auto issue_slice = [&](unsigned long long i) {
+        const int k = kb + (int)(i % (unsigned long long)(ke - kb));
+        float2* dst = tstream + (i & 1) * SL;
+        unsigned long long* bar = tbar + (i & 1);
+        // the buffer was last read by the generic proxy (every thread passed a barrier since)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if constexpr (FWD) {
+            const unsigned vb = 8u * L, ub = fbin ? 8u * 18 * T : 0u;
+            mbar_expect_tx(bar, vb + ub);
+            if (A.skip_copy) return;
+            bulk_g2s(dst, vtab + (size_t)k * L, vb, bar);
+            if (fbin) bulk_g2s(dst + L, fbtab + (size_t)k * 18 * T, ub, bar);
+        } else {
+            mbar_expect_tx(bar, 8u * 34 * T);
+            if (A.skip_copy) return;
+            bulk_g2s(dst, ubtab + (size_t)k * 18 * T, 8u * 18 * T, bar);
+            bulk_g2s(dst + 18 * T, vown + (size_t)k * 16 * T, 8u * 16 * T, bar);
+        }
+    };
+    if constexpr (STREAM) {
+        if (cfirst < ntiles && ke > kb)
+            nslices = (unsigned long long)((ntiles - cfirst + cstep - 1) / cstep) * (unsigned long long)(ke - kb);
+        if (threadIdx.x == 0) {
+            mbar_init(tbar, 1);
+            mbar_init(tbar + 1, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && nslices > 0) issue_slice(0);
+    }
 
     constexpr int NSTAGE = warp_nstage<LOG2L, STRIDED>();
     int cur = 0;
@@ -570,15 +670,32 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             }
         }
 
-        const int kb = (int)(((long long)rank * crank) / csize);
-        const int ke = (int)(((long long)rank * (crank + 1)) / csize);
+        if constexpr (BATCHED) {
+            kb = (int)(((long long)rank * crank) / csize);
+            ke = (int)(((long long)rank * (crank + 1)) / csize);
+        }
         for (int k = kb; k < ke; ++k) {
+            // streamed tables: wait for this term's slice (bounded), then, with every thread
+            // past the barrier and so done with the previous slice, fetch the next one into it
+            const float2* tsv = nullptr;  // forward v_k (L) / adjoint bin-ordered u_k (18 T)
+            const float2* tsu = nullptr;  // forward bin-ordered u_k (18 T) / adjoint lane-ordered v_k (16 T)
+            if constexpr (STREAM) {
+                const bool ok = mbar_wait(tbar + (slice & 1), (unsigned)((slice >> 1) & 1));
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) atomicOr(A.status, 1u);
+                    return;  // every thread: nothing of this CTA is in flight but the late copy
+                }
+                if (threadIdx.x == 0 && slice + 1 < nslices) issue_slice(slice + 1);
+                tsv = tstream + (slice & 1) * SL;
+                tsu = FWD ? tsv + L : tsv + 18 * T;
+                ++slice;
+            }
             Cx<float> x[16];
             if constexpr (FWD) {
                 const float2* vk = vtab + (size_t)k * L;
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
-                    float2 v = __ldg(vk + t + T * s);
+                    float2 v = STREAM ? tsv[t + T * s] : __ldg(vk + t + T * s);
                     const float a = VAL_SMEM ? aux[t + T * s] : val[s];
                     x[s] = Cx<float>{v.x * a, v.y * a};
                 }
@@ -592,8 +709,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 for (int s = 0; s < 16; ++s) {
                     Cx<float> z{0.0f, 0.0f};
                     if (s <= 8) {
-                        const float2 u0 = __ldg(ubk + (2 * s) * T + t);
-                        const float2 u1 = __ldg(ubk + (2 * s + 1) * T + t);
+                        const float2 u0 = STREAM ? tsv[(2 * s) * T + t] : __ldg(ubk + (2 * s) * T + t);
+                        const float2 u1 = STREAM ? tsv[(2 * s + 1) * T + t] : __ldg(ubk + (2 * s + 1) * T + t);
                         z.re = fmaf(u1.x, gb[2 * s + 1], u0.x * gb[2 * s]);
                         z.im = fmaf(u1.y, gb[2 * s + 1], u0.y * gb[2 * s]);
                     }
@@ -665,7 +782,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
             float2 post[FWD ? 1 : 16];
             if constexpr (!FWD) {
 #pragma unroll
-                for (int o = 0; o < 16; ++o) post[o] = __ldg(vown + ((size_t)k * 16 + o) * T + t);
+                for (int o = 0; o < 16; ++o) post[o] = STREAM ? tsu[o * T + t] : __ldg(vown + ((size_t)k * 16 + o) * T + t);
             }
             gsync<T, FT>(fl);
             Cx<float> y[16];  // step-B outputs in Own<> order
@@ -748,8 +865,8 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
 #pragma unroll
                 for (int c = 0; c < 9; ++c) {
                     const Cx<float> yc = y[fslot<LOG2L>(c)];
-                    const float2 u0 = __ldg(fbk + (2 * c) * T + t);
-                    const float2 u1 = __ldg(fbk + (2 * c + 1) * T + t);
+                    const float2 u0 = STREAM ? tsu[(2 * c) * T + t] : __ldg(fbk + (2 * c) * T + t);
+                    const float2 u1 = STREAM ? tsu[(2 * c + 1) * T + t] : __ldg(fbk + (2 * c + 1) * T + t);
                     acc[2 * c] = fmaf(u0.x, yc.re, fmaf(-u0.y, yc.im, acc[2 * c]));
                     acc[2 * c + 1] = fmaf(u1.x, yc.re, fmaf(-u1.y, yc.im, acc[2 * c + 1]));
                 }

@@ -359,3 +359,30 @@ def test_2d_long_axes_sampled(torch_dev, n):
     lhs = float((T.forward(to_dev(torch, dev, y, "fp32")).double().cpu().numpy() * alpha).sum())
     rhs = float((g * y).sum())
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(alpha) * np.linalg.norm(y)
+
+
+def test_bounded_wait_reports_timeout_and_the_context_survives(torch_dev):
+    """Failure detection without a fault: with the table copies withheld (the testing hook),
+    every CTA of the sweep waits about one second for its first table slice, records the
+    timeout in the plan's status word and returns; jt_plan_check reports JT_ETIMEOUT once, and
+    the same plan then transforms correctly."""
+    torch, dev = torch_dev
+    from paper_1901_07275_gb300 import binding as B
+
+    n, ab = (512,), [(0.3, -0.4)]
+    T = make(n, ab, "fp32")
+    T.set_ksplit(1)  # the single-CTA instance, which streams its tables
+    x = to_dev(torch, dev, syn.normal(91, 0, (8,) + n), "fp32")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert B.jt_plan_check(T._plan, stream) == B.JT_OK
+    B.jt_plan_inject_wait_timeout(T._plan, True)
+    try:
+        T.forward(x)
+        assert B.jt_plan_check(T._plan, stream) == B.JT_ETIMEOUT
+        assert B.jt_plan_check(T._plan, stream) == B.JT_OK  # cleared
+    finally:
+        B.jt_plan_inject_wait_timeout(T._plan, False)
+    f = T.forward(x)
+    assert B.jt_plan_check(T._plan, stream) == B.JT_OK
+    M = mats_for(n, ab)
+    assert rel(f.cpu().numpy(), oracle.forward(x.double().cpu().numpy(), M)) < TOL["fp32"]
