@@ -160,6 +160,8 @@ __device__ __forceinline__ Cx<dw> cmul(Cx<dw> a, Cx<dw> b) {
     return {sub_nr(mul_nr(a.re, b.re), mul_nr(a.im, b.im)), add_nr(mul_nr(a.re, b.im), mul_nr(a.im, b.re))};
 }
 __device__ __forceinline__ Cx<dw> cscale(Cx<dw> a, dw s) { return {mul_nr(a.re, s), mul_nr(a.im, s)}; }
+// Re(a b) added at once to a normalised accumulator by the full double-word sum
+__device__ __forceinline__ dw re_mul(Cx<dw> a, Cx<dw> b) { return sub_nr(mul_nr(a.re, b.re), mul_nr(a.im, b.im)); }
 
 // Butterfly sums and the products of the constant twiddles inside a DFT (unnormalised for
 // double-words).
@@ -449,6 +451,46 @@ struct BigAxisDev {
     dw* part = nullptr;            // max_ctas x n partial sums
 };
 
+// Bulk (TMA) copies of contiguous table slices into shared memory, completed on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// arrive once, announcing `bytes` of copies that complete on this barrier
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of `bar` with the given parity to complete, for at most about one second;
+// false if the wait ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it == 0) t0 = global_ns();
+        else if ((it & 63) == 0 && (global_ns() - t0 > 1000000000ull || it > (1u << 24))) return false;
+    }
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // ------------------------------------------------------------------ clusters
 // Rank split: the CTAs of one thread-block cluster share a tile of fibres, CTA c of S taking
 // the rank terms [rank c / S, rank (c + 1) / S), and add their partial sums through
@@ -584,6 +626,27 @@ struct Lean {
     static constexpr bool value = Shape<R, LOG2L>::THREADS >= 1024;
 };
 
+// Double-word sweeps of length 16..512 without a rank split stream each rank term's v_k (L)
+// and u_k (n) into shared memory with bulk copies, one term ahead: at 16 bytes an entry the
+// tables of a few rank terms already exceed what L1 keeps, and the loads right before use
+// waited on L2.
+template <class R, int LOG2L, bool SPLIT>
+struct DwStream {
+    static constexpr bool value = sizeof(R) == 8 && !SPLIT && LOG2L >= 4 && LOG2L <= 9;
+};
+
+template <class R, int LOG2L, bool SPLIT = false>
+constexpr size_t axis_smem_bytes() {
+    using S = Shape<R, LOG2L>;
+    const size_t base =
+        sizeof(R) * (size_t)S::G * S::GSTRIDE + (TwSmem<R, LOG2L>::value ? sizeof(Cx<R>) * (size_t)S::L : 0);
+    // streamed slices: two of 2 L complex (v_k, then u_k), 16-byte aligned, two mbarriers, and
+    // a copy of the bin pointers (L/2 + 2 ints) for the adjoint's scatter
+    return DwStream<R, LOG2L, SPLIT>::value
+               ? ((base + 15) & ~(size_t)15) + 2 * 2 * sizeof(Cx<R>) * (size_t)S::L + 16 + 4 * ((size_t)S::L / 2 + 2)
+               : base;
+}
+
 // CTAs of 256 threads are held to 128 registers a thread, so that two of them fit an SM.
 template <class R, int LOG2L, bool FWD, bool SPLIT = false>
 __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::THREADS <= 256) ? 2 : 1)
@@ -625,6 +688,62 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
     const long long ntiles = (nfib + G - 1) / G;
     const unsigned csize = SPLIT ? cluster_size() : 1u, crank = SPLIT ? cluster_rank() : 0u;
     const int kb = (int)(((long long)rank * crank) / csize), ke = (int)(((long long)rank * (crank + 1)) / csize);
+    const long long cfirst = SPLIT ? (long long)cluster_index() : (long long)blockIdx.x;
+    const long long cstep = SPLIT ? (long long)cluster_count() : (long long)gridDim.x;
+
+    // Streamed tables (DwStream): slice i (the i-th rank term this CTA applies, over all of its
+    // tiles) holds v_k then u_k, goes to buffer i & 1 and completes the ((i >> 1) + 1)-th phase
+    // of that buffer's mbarrier.  Thread 0 issues slice i + 1 once every thread has passed the
+    // barrier after slice i's wait, so nobody still reads the buffer it overwrites.
+    constexpr bool STREAM = DwStream<R, LOG2L, SPLIT>::value;
+    Cx<R>* tsl = nullptr;
+    unsigned long long* tbar = nullptr;
+    const int* bin_ptr = A.bin_ptr;
+    unsigned long long nslices = 0, slice = 0;
+    if constexpr (STREAM) {
+        const size_t off = (axis_smem_bytes<R, LOG2L, true>() + 15) & ~(size_t)15;
+        tsl = reinterpret_cast<Cx<R>*>(smem_raw + off);
+        tbar = reinterpret_cast<unsigned long long*>(tsl + 4 * L);
+        if constexpr (!FWD) {
+            int* sbp = reinterpret_cast<int*>(tbar + 2);
+            for (int i = threadIdx.x; i < L / 2 + 2; i += S::THREADS) sbp[i] = __ldg(A.bin_ptr + i);
+            bin_ptr = sbp;  // read by the adjoint's scatter after the barrier below
+        }
+        if (cfirst < ntiles && ke > kb)
+            nslices = (unsigned long long)((ntiles - cfirst + cstep - 1) / cstep) * (unsigned long long)(ke - kb);
+        if (threadIdx.x == 0) {
+            mbar_init(tbar, 1);
+            mbar_init(tbar + 1, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
+    auto issue_slice = [&](unsigned long long i) {
+        const int k = kb + (int)(i % (unsigned long long)(ke - kb));
+        Cx<R>* dst = tsl + (i & 1) * (2 * L);
+        unsigned long long* bar = tbar + (i & 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const unsigned vb = (unsigned)(sizeof(Cx<R>) * L), ub = (unsigned)(sizeof(Cx<R>) * n);
+        mbar_expect_tx(bar, vb + ub);
+        bulk_g2s(dst, vtab + (size_t)k * L, vb, bar);
+        bulk_g2s(dst + L, utab + (size_t)k * n, ub, bar);
+    };
+    // wait for this term's slice (bounded), then fetch the next; false if the wait ran out
+    auto next_slice = [&](const Cx<R>*& vk, const Cx<R>*& uk) -> bool {
+        const bool ok = mbar_wait(tbar + (slice & 1), (unsigned)((slice >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && A.status) atomicOr(A.status, 1u);
+            return false;
+        }
+        if (threadIdx.x == 0 && slice + 1 < nslices) issue_slice(slice + 1);
+        vk = tsl + (slice & 1) * (2 * L);
+        uk = vk + L;
+        ++slice;
+        return true;
+    };
+    if constexpr (STREAM) {
+        if (threadIdx.x == 0 && nslices > 0) issue_slice(0);
+    }
 
     int mj[LEAN ? 1 : E];  // forward: bins of the owned output points
     if constexpr (FWD && !LEAN) {
@@ -635,8 +754,6 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
         }
     }
 
-    const long long cfirst = SPLIT ? (long long)cluster_index() : (long long)blockIdx.x;
-    const long long cstep = SPLIT ? (long long)cluster_count() : (long long)gridDim.x;
     for (long long tile = cfirst; tile < ntiles; tile += cstep) {
         const long long f = tile * G + g;
         const bool valid = f < nfib;
@@ -672,6 +789,9 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
             for (int k = kb; k < ke; ++k) {
                 Cx<R> x[E];
                 const Cx<R>* vk = vtab + (size_t)k * L;
+                const Cx<R>* uk = utab + (size_t)k * n;
+                if constexpr (STREAM)
+                    if (!next_slice(vk, uk)) return;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     if constexpr (LEAN)
@@ -688,7 +808,6 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                     if (m <= L / 2) xb.template put<S>(m, x[e]);
                 }
                 group_sync<T, G>(g);
-                const Cx<R>* uk = utab + (size_t)k * n;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     int j = t + T * e;
@@ -722,23 +841,25 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
             group_sync<T, G>(g);
             for (int k = kb; k < ke; ++k) {
                 const Cx<R>* uk = utab + (size_t)k * n;
+                const Cx<R>* vk = vtab + (size_t)k * L;
+                if constexpr (STREAM)
+                    if (!next_slice(vk, uk)) return;
                 Cx<R> x[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     int m = t + T * e;
                     Cx<R> z{RealOps<R>::zero(), RealOps<R>::zero()};
                     if (m <= L / 2) {
-                        int p1 = __ldg(A.bin_ptr + m), p2 = __ldg(A.bin_ptr + m + 1);
+                        int p1 = bin_ptr[m], p2 = bin_ptr[m + 1];
                         for (int p = p1; p < p2; ++p) {
                             const int j = A.sorted ? p : __ldg(A.bin_idx + p);  // sorted: identity
-                            z = z + cscale(uk[j], aux[j]);
+                            z = bf_add(z, cscale(uk[j], aux[j]));
                         }
                     }
                     x[e] = z;
                 }
                 group_sync<T, G>(g);  // previous FFT done with the buffer
                 fft<R, LOG2L>(x, sre, sim, tw, t, g);
-                const Cx<R>* vk = vtab + (size_t)k * L;
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc[e] = acc[e] + re_mul(vk[t + T * e], x[e]);
             }
@@ -828,11 +949,6 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
     }
 }
 
-template <class R, int LOG2L>
-constexpr size_t axis_smem_bytes() {
-    using S = Shape<R, LOG2L>;
-    return sizeof(R) * (size_t)S::G * S::GSTRIDE + (TwSmem<R, LOG2L>::value ? sizeof(Cx<R>) * (size_t)S::L : 0);
-}
 
 }  // namespace dev
 }  // namespace jt

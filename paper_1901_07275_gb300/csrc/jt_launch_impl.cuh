@@ -18,7 +18,7 @@ cudaError_t generic_launch_one(const dev::AxisDev& A, bool fwd, const typename d
                                typename dev::RealOps<R>::io* out, long long nfib, long long inner, int ksplit,
                                cudaStream_t s) {
     using S = dev::Shape<R, LOG2L>;
-    constexpr size_t smem = dev::axis_smem_bytes<R, LOG2L>();
+    constexpr size_t smem = dev::axis_smem_bytes<R, LOG2L, SPLIT>();
     const long long ntiles = (nfib + S::G - 1) / S::G;
     if (fwd)
         return launch_tiles(generic_info<R, LOG2L, true, SPLIT>(), dev::axis_kernel<R, LOG2L, true, SPLIT>, S::THREADS,
