@@ -51,3 +51,12 @@ def test_algorithmic_counts():
     b = bench.axis_table_bytes(512, 512, 10, 27, 4)
     assert b == 10 * 512 * 8 + 10 * 512 * 8 + 4 * 512 + 27 * 512 * 4 + 512 * 8 + 4 * (256 + 2) + 4 * 512
     assert bench.aggregate(2, 1000.0, 5, 10.0) == pytest.approx(2 * 1000.0 * 5 / 0.010)
+
+
+def test_double_word_flops_per_real_operation():
+    """The split roofline's count: a real sum costs SloppyDWPlusDW's 11 FP32 operations, a real
+    product the FMA-based DWTimesDW's 9 operations of which 3 are FMAs (12 flops), and the FFT
+    count 5 L log2 L is 6 sums to 4 products (a radix-2 butterfly)."""
+    sums, products = 6, 4
+    assert bench.DW_FLOPS_PER_FLOP == pytest.approx((sums * 11 + products * (9 + 3)) / (sums + products))
+    assert bench.DW_FLOPS_PER_FLOP == pytest.approx(11.4)
