@@ -140,9 +140,23 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     }
     std::vector<Cx<R>> twid(L);
     const double twopi = 6.283185307179586476925286766559;
-    for (int64_t q = 0; q < L; ++q) {
-        double ang = twopi * (double)q / (double)L;
-        twid[q] = Cx<R>{to_r(std::cos(ang), tag), to_r(std::sin(ang), tag)};
+    if (std::is_same<R, float>::value && ax.log2L > jt::F32_WARP_MAX_LOG2L) {
+        // FP32 Stockham axes longer than 4096: the twiddles in pass order, pass of span NS
+        // (R0, 16 R0, 256 R0) at [NS - R0 + (r - 1) NS + k] = e^{2 pi i r k / (16 NS)}, r = 1..15,
+        // k < NS, so that the lanes of a pass read consecutive entries
+        const int P = (ax.log2L + 3) / 4;
+        const int64_t R0 = (int64_t)1 << (ax.log2L - 4 * (P - 1));
+        for (int64_t ns = R0; ns < L; ns *= 16)
+            for (int64_t i = 0; i < 15 * ns; ++i) {
+                const int64_t r = 1 + i / ns, k = i % ns;
+                double ang = twopi * (double)(r * k) / (double)(16 * ns);
+                twid[ns - R0 + i] = Cx<R>{to_r(std::cos(ang), tag), to_r(std::sin(ang), tag)};
+            }
+    } else {
+        for (int64_t q = 0; q < L; ++q) {
+            double ang = twopi * (double)q / (double)L;
+            twid[q] = Cx<R>{to_r(std::cos(ang), tag), to_r(std::sin(ang), tag)};
+        }
     }
     // bins: points of bin m are bin_idx[bin_ptr[m] .. bin_ptr[m+1]), m = 0..L/2
     std::vector<int> bin_ptr(L / 2 + 2, 0), bin_idx(n);

@@ -360,11 +360,20 @@ struct Shape {
     static constexpr int GSTRIDE = ((2 * PADL + L) + 1) & ~1;
 };
 
-// Double-word instances up to L = 2048 read their twiddles from a per-CTA copy in shared
-// memory instead of the (L1-cached) table: every rank term of every fibre re-reads them.
+// FP32 axes longer than 4096 (the Stockham kernel's long instances) get their twiddle table
+// in pass order from the plan: at [NS - R0 + (r - 1) NS + k] the twiddle e^{2 pi i r k / (16 NS)}
+// of the pass of span NS, so that the 32 lanes of a pass read 32 consecutive entries (in
+// natural order they read one 32-byte sector each, and the table missed L1).
+template <class R, int LOG2L>
+struct TwPass {
+    static constexpr bool value = sizeof(R) == 4 && LOG2L >= 13;
+};
+// Double-word instances up to L = 2048, and FP32 at L = 8192, read their twiddles from a
+// per-CTA copy in shared memory instead of the (L1-cached) table: every rank term of every
+// fibre re-reads them.
 template <class R, int LOG2L>
 struct TwSmem {
-    static constexpr bool value = sizeof(R) == 8 && LOG2L >= 1 && LOG2L <= 11;
+    static constexpr bool value = (sizeof(R) == 8 && LOG2L >= 1 && LOG2L <= 11) || (sizeof(R) == 4 && LOG2L == 13);
 };
 
 // The exchange buffer of one group: (re, im) arrays for FP32, interleaved complex double-words.
@@ -404,7 +413,7 @@ struct AxisDev {
     const void* utab;    // rank x n   Cx<R>: sqrt(w_j) u_k[j]
     const int* mtab;     // n          FFT bin of point j
     const void* vblk;    // nu0 x n    R:     sqrt(w_j) P~_c(t_j)
-    const void* twid;    // L          Cx<R>: e^{+2 pi i s / L}
+    const void* twid;    // L          Cx<R>: e^{+2 pi i s / L} (TwPass axes: in Stockham pass order)
     const int* bin_ptr;  // L/2 + 2    points of bin m: bin_idx[bin_ptr[m] .. bin_ptr[m+1])
     const int* bin_idx;  // n
     // FP32 warp kernel only: u_k in bin order, rank x 9 x 2 x T complex; entry
@@ -582,7 +591,7 @@ __device__ __forceinline__ void stockham_pass(Cx<R>* x, R* sre, R* sim, const Cx
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < RX; ++r) {
-                if constexpr (TwSmem<R, LOG2L>::value)  // per-pass table: [NS - R0 + (r - 1) NS + k]
+                if constexpr (TwSmem<R, LOG2L>::value || TwPass<R, LOG2L>::value)  // [NS - R0 + (r - 1) NS + k]
                     a[r] = cmul(a[r], tw[(NS - S::R0) + (r - 1) * NS + k]);
                 else
                     a[r] = cmul(a[r], tw[(r * k) * (L / (NS * RX))]);
@@ -677,11 +686,15 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
         // w_L^{r k L / (8 NS)}, r = 1..7, k < NS, at [NS - R0 + (r - 1) NS + k]: the lanes of a
         // pass read consecutive k, so the reads of a quarter-warp hit different banks
         Cx<R>* tws = reinterpret_cast<Cx<R>*>(smem + (size_t)G * S::GSTRIDE);
-        for (int ns = S::R0; ns < L; ns *= S::EMAX)
-            for (int i = threadIdx.x; i < (S::EMAX - 1) * ns; i += S::THREADS) {
-                const int r = 1 + i / ns, k = i % ns;
-                tws[ns - S::R0 + i] = tw[((r * k) * (L / (ns * S::EMAX))) & (L - 1)];
-            }
+        if constexpr (TwPass<R, LOG2L>::value) {
+            for (int i = threadIdx.x; i < L - S::R0; i += S::THREADS) tws[i] = tw[i];
+        } else {
+            for (int ns = S::R0; ns < L; ns *= S::EMAX)
+                for (int i = threadIdx.x; i < (S::EMAX - 1) * ns; i += S::THREADS) {
+                    const int r = 1 + i / ns, k = i % ns;
+                    tws[ns - S::R0 + i] = tw[((r * k) * (L / (ns * S::EMAX))) & (L - 1)];
+                }
+        }
         __syncthreads();
         tw = tws;
     }

@@ -47,8 +47,10 @@ struct WShape {
     static constexpr int BUF0 = (XBUF > YBUF ? XBUF : YBUF);
     static constexpr int BUF = (BUF0 > X2BUF ? BUF0 : X2BUF);
     static constexpr int AUX = L + L / 32 + 1;                  // per fibre: alpha_V / g (floats)
-    // T >= 64: the step-A twiddles w_L^{t k1} (k1 = 1..15) live in shared memory, [k1-1][t]
-    static constexpr int TWS = (T >= 64) ? 15 * T + 15 * R : 0;  // float2 (+ step-B twiddles)
+    // T >= 64: the step-A twiddles w_L^{t k1} for k1 = 1, 2, 4, 8 live in shared memory,
+    // [log2 k1][t], then the step-B twiddles w_T^{h k2} for k2 = 1, 2, 4, 8 at [4 T + log2 k2][h];
+    // the other powers are formed from them (apply_powers15)
+    static constexpr int TWS = (T >= 64) ? 4 * T + 4 * R : 0;  // float2
     // staging tile rows: consecutive threads cover FT fibres x (32 / FT) rows
     static constexpr int TROW = L + ((FT >= 32) ? 1 : 32 / FT);
     // gather buffer index: a half-warp writes runs m0 + [0, 8) and m0 + 128 + [0, 8)
@@ -169,6 +171,31 @@ __host__ __device__ constexpr int fslot(int c) {
     return (c < 8) ? (c / (S::R / 2)) * S::R + c % (S::R / 2) : S::R / 2;
 }
 
+// x[k] *= w^k for k = 1..15, with w^k read from a table only for k = 1, 2, 4, 8 (at
+// tab[log2(k) stride]) and the other eleven powers formed as products of two of those (or of
+// earlier products): 4 shared-memory reads and 11 extra complex products instead of 15 reads.
+// Each derived power carries at most three table roundings and two product roundings.
+__device__ __forceinline__ void apply_powers15(Cx<float>* x, const float2* tab, int stride) {
+    const Cx<float> w1 = cx(tab[0]), w2 = cx(tab[stride]), w4 = cx(tab[2 * stride]), w8 = cx(tab[3 * stride]);
+    x[1] = cmul(x[1], w1);
+    x[2] = cmul(x[2], w2);
+    x[4] = cmul(x[4], w4);
+    x[8] = cmul(x[8], w8);
+    const Cx<float> w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4);
+    x[3] = cmul(x[3], w3);
+    x[5] = cmul(x[5], w5);
+    x[6] = cmul(x[6], w6);
+    x[9] = cmul(x[9], cmul(w1, w8));
+    x[10] = cmul(x[10], cmul(w2, w8));
+    x[12] = cmul(x[12], cmul(w4, w8));
+    const Cx<float> w7 = cmul(w3, w4);
+    x[7] = cmul(x[7], w7);
+    x[11] = cmul(x[11], cmul(w3, w8));
+    x[13] = cmul(x[13], cmul(w5, w8));
+    x[14] = cmul(x[14], cmul(w6, w8));
+    x[15] = cmul(x[15], cmul(w7, w8));
+}
+
 // Sum CNT values per lane over the lanes of a group (xor offsets OFF, OFF/2, .., 1) so that
 // each lane keeps a share: at every step the lanes with that offset bit set keep the upper
 // half of their live values and add the partner's copy of it, so after log2(CNT) steps lane u
@@ -260,14 +287,14 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
     constexpr bool TW_SMEM = S::TWS > 0;
     Cx<float> twA[TW_SMEM ? 1 : 16];
     if constexpr (TW_SMEM) {
-        // [k1-1][t] = w_L^{t k1}, then the step-B twiddles [k2-1][h] = w_L^{16 h k2}
-        for (int i = threadIdx.x; i < 15 * T; i += S::THREADS) {
-            const int k1 = 1 + i / T, tt = i % T;
+        // [b][t] = w_L^{t 2^b}, then the step-B twiddles [4 T + b][h] = w_L^{16 h 2^b}, b < 4
+        for (int i = threadIdx.x; i < 4 * T; i += S::THREADS) {
+            const int k1 = 1 << (i / T), tt = i % T;
             twS[i] = __ldg(tw + ((tt * k1) & (L - 1)));
         }
-        for (int i = threadIdx.x; i < 15 * S::R; i += S::THREADS) {
-            const int k2 = 1 + i / S::R, hh = i % S::R;
-            twS[15 * T + i] = __ldg(tw + ((16 * hh * k2) & (L - 1)));
+        for (int i = threadIdx.x; i < 4 * S::R; i += S::THREADS) {
+            const int k2 = 1 << (i / S::R), hh = i % S::R;
+            twS[4 * T + i] = __ldg(tw + ((16 * hh * k2) & (L - 1)));
         }
     } else {
 #pragma unroll
@@ -727,12 +754,11 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
                 dft<16, float>(x);
             else
                 dft16_low9<float>(x);
+            if constexpr (TW_SMEM) {
+                apply_powers15(x, twS + t, T);
+            } else {
 #pragma unroll
-            for (int k1 = 1; k1 < 16; ++k1) {
-                if constexpr (TW_SMEM)
-                    x[k1] = cmul(x[k1], cx(twS[(k1 - 1) * T + t]));
-                else
-                    x[k1] = cmul(x[k1], twA[k1]);
+                for (int k1 = 1; k1 < 16; ++k1) x[k1] = cmul(x[k1], twA[k1]);
             }
             // exchange: buf[k1][t]
             gsync<T, FT>(fl);
@@ -790,8 +816,7 @@ __global__ void __launch_bounds__(WShape<LOG2L>::THREADS, JT_WARP_MINB)
 #pragma unroll
                 for (int q = 0; q < 16; ++q) a[q] = cx(buf[k1 * S::XROW + R * q + h]);
                 dft<16, float>(a);
-#pragma unroll
-                for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], cx(twS[15 * T + (k2 - 1) * R + h]));
+                apply_powers15(a, twS + 4 * T + h, R);
                 gsync<T, FT>(fl);
 #pragma unroll
                 for (int k2 = 0; k2 < 16; ++k2) buf[S::x2idx(k1, k2, h)] = f2(a[k2]);
