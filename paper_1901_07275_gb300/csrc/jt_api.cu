@@ -172,6 +172,21 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     std::vector<Cx<R>> ubtab, ovu, vown, fbtab;
     std::vector<int> bjtab, ovftab, ovj, bjf;
     int ovmode = 0, ovmax = 0, fbin = 0;
+    auto fill_ubtab = [&](int64_t TT) {
+        ubtab.assign((size_t)r * 18 * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
+        for (int64_t k = 0; k < r; ++k)
+            for (int64_t s2 = 0; s2 <= 8; ++s2)
+                for (int64_t t = 0; t < TT; ++t) {
+                    const int64_t m = t + TT * s2;
+                    if (m > L / 2) continue;
+                    for (int i = 0; i < 2; ++i) {
+                        const int64_t p = bin_ptr[m] + i;
+                        if (p >= bin_ptr[m + 1]) break;
+                        const int64_t j = bin_idx[p];
+                        ubtab[(size_t)k * 18 * TT + (s2 * 2 + i) * TT + t] = utab[(size_t)k * n + j];
+                    }
+                }
+    };
     if (std::is_same<R, float>::value && jt::f32_warp_path(ax.log2L)) {
         const int64_t TT = L / 16;
         // v_k in the adjoint's output order: [k][o][t] = v_k[Own(t, o)], coalesced per slot
@@ -242,19 +257,22 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
                 bjf.clear();
             }
         }
-        ubtab.assign((size_t)r * 18 * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
-        for (int64_t k = 0; k < r; ++k)
-            for (int64_t s2 = 0; s2 <= 8; ++s2)
-                for (int64_t t = 0; t < TT; ++t) {
-                    const int64_t m = t + TT * s2;
-                    if (m > L / 2) continue;
-                    for (int i = 0; i < 2; ++i) {
-                        const int64_t p = bin_ptr[m] + i;
-                        if (p >= bin_ptr[m + 1]) break;
-                        const int64_t j = bin_idx[p];
-                        ubtab[(size_t)k * 18 * TT + (s2 * 2 + i) * TT + t] = utab[(size_t)k * n + j];
-                    }
-                }
+        fill_ubtab(TT);
+    } else if (std::is_same<R, float>::value && ax.log2L > jt::F32_WARP_MAX_LOG2L) {
+        // FP32 Stockham axes longer than 4096 (threads of T = L / 16, bins m = t + T e): the
+        // adjoint's bin-ordered tables, and per thread a flag for a bin with more than two points
+        const int64_t TT = L / 16;
+        bjtab.assign((size_t)18 * TT, -1);
+        ovftab.assign((size_t)2 * TT, 0);
+        for (int64_t s2 = 0; s2 <= 8; ++s2)
+            for (int64_t t = 0; t < TT; ++t) {
+                const int64_t m = t + TT * s2;
+                if (m > L / 2) continue;
+                for (int i = 0; i < 2; ++i)
+                    if (bin_ptr[m] + i < bin_ptr[m + 1]) bjtab[(s2 * 2 + i) * TT + t] = bin_idx[bin_ptr[m] + i];
+                if (bin_ptr[m + 1] - bin_ptr[m] > 2) ovftab[2 * t] = 1;
+            }
+        fill_ubtab(TT);
     }
     AxisDev& A = ax.dev;
     A.n = (int)n;

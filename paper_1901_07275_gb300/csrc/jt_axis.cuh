@@ -364,6 +364,14 @@ struct Shape {
 // in pass order from the plan: at [NS - R0 + (r - 1) NS + k] the twiddle e^{2 pi i r k / (16 NS)}
 // of the pass of span NS, so that the 32 lanes of a pass read 32 consecutive entries (in
 // natural order they read one 32-byte sector each, and the table missed L1).
+// The FP32 long instances' adjoint gathers each bin's first two points from a bin-ordered copy
+// of u_k and a bin-ordered point table (AxisDev ubtab / bjtab, the layout of the four-step
+// kernel with T = L / 16) instead of walking the CSR lists: in the walk every bin's loads
+// waited on the previous bin's, one L2 round trip after another.
+template <class R, int LOG2L>
+struct BinOrd {
+    static constexpr bool value = sizeof(R) == 4 && LOG2L >= 13;
+};
 template <class R, int LOG2L>
 struct TwPass {
     static constexpr bool value = sizeof(R) == 4 && LOG2L >= 13;
@@ -701,6 +709,9 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
     const long long ntiles = (nfib + G - 1) / G;
     const unsigned csize = SPLIT ? cluster_size() : 1u, crank = SPLIT ? cluster_rank() : 0u;
     const int kb = (int)(((long long)rank * crank) / csize), ke = (int)(((long long)rank * (crank + 1)) / csize);
+    // degrees of the dense block this CTA adds: its share of 0..nu0-1 (all of them without a
+    // rank split), so that no CTA of a cluster waits for one that does the whole block
+    const int cb0 = (int)(((long long)nu0 * crank) / csize), cb1 = (int)(((long long)nu0 * (crank + 1)) / csize);
     const long long cfirst = SPLIT ? (long long)cluster_index() : (long long)blockIdx.x;
     const long long cstep = SPLIT ? (long long)cluster_count() : (long long)gridDim.x;
 
@@ -758,6 +769,9 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
         if (threadIdx.x == 0 && nslices > 0) issue_slice(0);
     }
 
+    // BinOrd adjoint: whether one of this thread's bins holds more than two points
+    bool binx = false;
+    if constexpr (BinOrd<R, LOG2L>::value && !FWD) binx = __ldg(A.ovftab + 2 * t) != 0;
     int mj[LEAN ? 1 : E];  // forward: bins of the owned output points
     if constexpr (FWD && !LEAN) {
 #pragma unroll
@@ -831,9 +845,11 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                     }
                 }
             }
-            // dense block: acc_j += sum_{c < nu0} sqrt(w_j) P~_c(t_j) alpha_c (first CTA of a cluster)
-            if (!SPLIT || crank == 0) {
-                for (int c = 0; c < nu0; ++c) {
+            // dense block: acc_j += sum_{c < nu0} sqrt(w_j) P~_c(t_j) alpha_c (a rank-split
+            // cluster shares the degrees out over its CTAs; the partial sums are added anyway)
+            {
+#pragma unroll 4
+                for (int c = cb0; c < cb1; ++c) {
                     R ac = aux[c];
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
@@ -852,43 +868,90 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                 }
             }
             group_sync<T, G>(g);
+            // BinOrd: g at the first two points of each owned bin m = t + T e (e <= 8), from the
+            // bin-ordered point table (-1: none), held for the whole tile unless LEAN
+            constexpr bool BINORD = BinOrd<R, LOG2L>::value;
+            R gb[(BINORD && !LEAN) ? 18 : 1];
+            if constexpr (BINORD && !LEAN) {
+#pragma unroll
+                for (int q = 0; q < 18; ++q) {
+                    const int j = __ldg(A.bjtab + q * T + t);
+                    gb[q] = (j >= 0) ? aux[j] : RealOps<R>::zero();
+                }
+            }
             for (int k = kb; k < ke; ++k) {
                 const Cx<R>* uk = utab + (size_t)k * n;
                 const Cx<R>* vk = vtab + (size_t)k * L;
                 if constexpr (STREAM)
                     if (!next_slice(vk, uk)) return;
                 Cx<R> x[E];
+                if constexpr (BINORD) {
+                    // z[m] = u_k g at the bin's first two points (u_k in bin order, so that no
+                    // load waits on another), plus the rest of the bin from the CSR lists on
+                    // the lanes flagged as owning a bin with more than two points
+                    const Cx<R>* ubk = reinterpret_cast<const Cx<R>*>(A.ubtab) + (size_t)k * (18 * T);
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    int m = t + T * e;
-                    Cx<R> z{RealOps<R>::zero(), RealOps<R>::zero()};
-                    if (m <= L / 2) {
-                        int p1 = bin_ptr[m], p2 = bin_ptr[m + 1];
-                        for (int p = p1; p < p2; ++p) {
-                            const int j = A.sorted ? p : __ldg(A.bin_idx + p);  // sorted: identity
-                            z = bf_add(z, cscale(uk[j], aux[j]));
+                    for (int e = 0; e < E; ++e) {
+                        Cx<R> z{RealOps<R>::zero(), RealOps<R>::zero()};
+                        if (e <= 8) {
+                            const Cx<R> u0 = ubk[(2 * e) * T + t], u1 = ubk[(2 * e + 1) * T + t];
+                            R g0, g1;
+                            if constexpr (LEAN) {
+                                const int j0 = __ldg(A.bjtab + (2 * e) * T + t), j1 = __ldg(A.bjtab + (2 * e + 1) * T + t);
+                                g0 = (j0 >= 0) ? aux[j0] : RealOps<R>::zero();
+                                g1 = (j1 >= 0) ? aux[j1] : RealOps<R>::zero();
+                            } else {
+                                g0 = gb[2 * e];
+                                g1 = gb[2 * e + 1];
+                            }
+                            z.re = u0.re * g0 + u1.re * g1;
+                            z.im = u0.im * g0 + u1.im * g1;
+                            if (binx) {
+                                const int m = t + T * e;
+                                if (m <= L / 2) {
+                                    const int p2 = __ldg(bin_ptr + m + 1);
+                                    for (int p = __ldg(bin_ptr + m) + 2; p < p2; ++p) {
+                                        const int j = A.sorted ? p : __ldg(A.bin_idx + p);
+                                        z = bf_add(z, cscale(uk[j], aux[j]));
+                                    }
+                                }
+                            }
                         }
+                        x[e] = z;
                     }
-                    x[e] = z;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        int m = t + T * e;
+                        Cx<R> z{RealOps<R>::zero(), RealOps<R>::zero()};
+                        if (m <= L / 2) {
+                            int p1 = bin_ptr[m], p2 = bin_ptr[m + 1];
+                            for (int p = p1; p < p2; ++p) {
+                                const int j = A.sorted ? p : __ldg(A.bin_idx + p);  // sorted: identity
+                                z = bf_add(z, cscale(uk[j], aux[j]));
+                            }
+                        }
+                        x[e] = z;
+                    }
                 }
                 group_sync<T, G>(g);  // previous FFT done with the buffer
                 fft<R, LOG2L>(x, sre, sim, tw, t, g);
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc[e] = acc[e] + re_mul(vk[t + T * e], x[e]);
             }
-            // dense block: alpha_c = sum_j sqrt(w_j) P~_c(t_j) g_j for c < nu0 (first CTA of a
-            // cluster), DB degrees at a time: every thread's partial sums over its points go to
+            // dense block: alpha_c = sum_j sqrt(w_j) P~_c(t_j) g_j for c < nu0 (a rank-split
+            // cluster shares the degrees out over its CTAs), DB degrees at a time: every thread's partial sums over its points go to
             // red[i][t] in the group's FFT buffer (DB T <= 2 PADL reals), a tree over t adds them
             // up with log2 T barriers for all DB degrees together, and element c is owned by
             // thread c % T at e = c / T.  Groups of 512 or more threads take 8 degrees at a time
             // (fewer barriers of the whole CTA); smaller groups one (more degrees at a time cost
             // them registers and occupancy).
-            if (!SPLIT || crank == 0) {
+            {
                 constexpr int DB0 = (T >= 512) ? 8 : 1;
                 constexpr int DB = (2 * S::PADL / T < DB0) ? 2 * S::PADL / T : DB0;
                 static_assert(DB >= 1 && DB * T <= 2 * S::PADL, "dense-block partials fit the FFT buffer");
                 R* red = sre;
-                for (int c0 = 0; c0 < nu0; c0 += DB) {
+                for (int c0 = cb0; c0 < cb1; c0 += DB) {
                     R part[DB];
 #pragma unroll
                     for (int i = 0; i < DB; ++i) part[i] = RealOps<R>::zero();
@@ -899,7 +962,7 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                             const R gj = LEAN ? aux[j] : val[e];
 #pragma unroll
                             for (int i = 0; i < DB; ++i)
-                                if (c0 + i < nu0) part[i] = part[i] + vblk[(size_t)(c0 + i) * n + j] * gj;
+                                if (c0 + i < cb1) part[i] = part[i] + vblk[(size_t)(c0 + i) * n + j] * gj;
                         }
                     }
                     group_sync<T, G>(g);  // the buffer is free (last FFT pass, previous degrees)
@@ -916,7 +979,7 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
 #pragma unroll
                     for (int i = 0; i < DB; ++i) {
                         const int c = c0 + i;
-                        if (c < nu0) {
+                        if (c < cb1) {
                             const R tot = red[i * T];
 #pragma unroll
                             for (int e = 0; e < E; ++e)

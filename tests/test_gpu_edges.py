@@ -1,7 +1,8 @@
 """Edge cases of the fused path against the oracle: the split degree nu0 at its limits, the
 shortest FFT lengths on strided axes (16 and 32, where the staging is single-buffered or
 the tile holds up to 256 fibres), 3-D transforms with a rank split on every axis, the
-double-word kernel at L = 8192 with a rank split, and ragged tiles."""
+double-word kernel at L = 8192 with a rank split, ragged tiles, and a long FP32 axis at crowded
+nonuniform points."""
 
 import numpy as np
 import pytest
@@ -130,3 +131,30 @@ def test_nonuniform_crowded_bins(torch_dev, cluster):
     M = [oracle.axis_matrix(n, *ab[0], t)]
     assert rel(T.forward(x).double().cpu().numpy(), oracle.forward(alpha, M)) < TOL["fp32"]
     assert rel(T.adjoint(x).double().cpu().numpy(), oracle.adjoint(alpha, M)) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("order,ks", [("sorted", 1), ("shuffled", 8)])
+def test_long_fp32_axis_nonuniform_crowded(torch_dev, order, ks):
+    """An FP32 axis of L = 8192 (the Stockham kernel's long instances) at nonuniform angles:
+    about one bin in five holds more than two points and one holds 40, the points come sorted
+    or shuffled (so that the bins' lists are walked through bin_idx), without a rank split and
+    with one of 8 (the dense block then shared over the cluster).  The forward on sampled rows
+    (all of the crowded bin among them) and the adjoint through them, against the oracle's J."""
+    torch, dev = torch_dev
+    n = 6000
+    t = np.concatenate([np.pi * syn.uniform(1800, 2, (n - 40,)), 1.0 + 1e-4 * syn.uniform(1801, 2, (40,))])
+    t = np.sort(t) if order == "sorted" else t[np.argsort(syn.uniform(1802, 2, (n,)))]
+    ab = [(0.3, -0.2)]
+    T = make((n,), ab, "fp32", points=[t])
+    assert T.fft_lens == [8192]
+    T.set_ksplit(ks)
+    alpha = syn.normal(1803, 0, (4, n))
+    f = T.forward(torch.tensor(alpha, dtype=torch.float32, device=dev)).double().cpu().numpy()
+    crowd = np.nonzero((t >= 1.0) & (t <= 1.0 + 1e-4))[0]
+    rows = np.union1d(np.unique(syn.integers(1804, 3, 96, 0, n)), np.concatenate([crowd, [0, n - 1]]))
+    Q = oracle.nonuniform_matrix(t[rows], ab[0][0], ab[0][1], n)
+    assert rel(f[:, rows], alpha @ Q.T) < TOL["fp32"]
+    g = np.zeros((2, n))
+    g[:, rows] = syn.normal(1805, 0, (2, rows.size))
+    a = T.adjoint(torch.tensor(g, dtype=torch.float32, device=dev)).double().cpu().numpy()
+    assert rel(a, g[:, rows] @ Q) < TOL["fp32"]
