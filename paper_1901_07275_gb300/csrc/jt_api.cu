@@ -523,16 +523,21 @@ jt_status tune_plan(jt_plan* plan, int64_t nrhs, cudaStream_t s) {
 // length 16..4096 run as one launch per group (at most BATCH_MAX_JOBS jobs a launch); every
 // other sweep is launched on its own.  The launches of a stage are spread over a few worker
 // streams (forked from and joined back to the caller's stream, with a barrier between
-// stages), so that small launches run side by side.  Nothing is allocated or copied at
-// execution, so an execution can be captured in a CUDA graph.
+// stages), so that small launches run side by side.  First-stage launches of one-dimensional
+// transforms only (nothing later waits for them) go to two more streams of the highest
+// priority that take no part in the stage barriers: those are mostly long axes with few
+// fibres, whose few CTAs then start at once and run beside the large groups instead of
+// holding up the next stage.  Nothing is allocated or copied at execution, so an execution
+// can be captured in a CUDA graph.
 struct jt_batch {
-    static constexpr int WORKERS = 4;
+    static constexpr int WORKERS = 4, FREE = 2, STREAMS = WORKERS + FREE;
     int count = 0;
     int prec = JT_FP32;
     std::vector<jt_plan*> plans;
     std::vector<int64_t> nrhs;
     struct Launch {
         bool fused = false;
+        bool free = false;  // on a free stream (index WORKERS + f): no stage barrier
         int stage = 0, log2L = 0, ksplit = 1, worker = 0;
         bool strided = false;
         // fused: device jobs [job_off, job_off + njobs), slot -> transform index
@@ -546,8 +551,8 @@ struct jt_batch {
     };
     std::vector<Launch> launches[2];  // [0] forward, [1] adjoint; ordered by stage
     jt::dev::BatchJob* d_jobs = nullptr;
-    cudaStream_t work[WORKERS] = {};
-    cudaEvent_t ev_fork = nullptr, ev_stage[WORKERS] = {}, ev_join[WORKERS] = {};
+    cudaStream_t work[STREAMS] = {};
+    cudaEvent_t ev_fork = nullptr, ev_stage[WORKERS] = {}, ev_join[STREAMS] = {};
 };
 
 namespace {
@@ -563,9 +568,9 @@ jt_status batch_run(jt_batch* b, const void* const* in, void* const* out, bool f
     if (!b || !in || !out) return JT_EINVAL;
     for (int i = 0; i < b->count; ++i)
         if (!in[i] || !out[i]) return JT_EINVAL;
-    constexpr int W = jt_batch::WORKERS;
+    constexpr int W = jt_batch::WORKERS, NS = jt_batch::STREAMS;
     if (cudaEventRecord(b->ev_fork, s) != cudaSuccess) return JT_ECUDA;
-    for (int w = 0; w < W; ++w)
+    for (int w = 0; w < NS; ++w)
         if (cudaStreamWaitEvent(b->work[w], b->ev_fork, 0) != cudaSuccess) return JT_ECUDA;
     int stage = 0;
     for (const auto& L : b->launches[fwd ? 0 : 1]) {
@@ -595,7 +600,7 @@ jt_status batch_run(jt_batch* b, const void* const* in, void* const* out, bool f
         }
         if (e != cudaSuccess) return JT_ECUDA;
     }
-    for (int w = 0; w < W; ++w) {
+    for (int w = 0; w < NS; ++w) {
         if (cudaEventRecord(b->ev_join[w], b->work[w]) != cudaSuccess) return JT_ECUDA;
         if (cudaStreamWaitEvent(s, b->ev_join[w], 0) != cudaSuccess) return JT_ECUDA;
     }
@@ -603,7 +608,8 @@ jt_status batch_run(jt_batch* b, const void* const* in, void* const* out, bool f
 }
 
 // Launch lists of one direction: groups per stage, then the stage's launches spread over the
-// workers, largest first, each to the least loaded worker.
+// workers, largest first, each to the least loaded worker (first-stage launches of 1-D
+// transforms only over the free streams the same way).
 void batch_plan_launches(jt_batch* b, bool fwd, const std::vector<SweepJob>& sweeps, int max_stage,
                          std::vector<jt::dev::BatchJob>& hjobs) {
     auto& out = b->launches[fwd ? 0 : 1];
@@ -656,10 +662,19 @@ void batch_plan_launches(jt_batch* b, bool fwd, const std::vector<SweepJob>& swe
             ls.push_back(L);
         }
         std::stable_sort(ls.begin(), ls.end(), [](const jt_batch::Launch& x, const jt_batch::Launch& y) { return x.cost > y.cost; });
-        double load[jt_batch::WORKERS] = {};
+        double load[jt_batch::STREAMS] = {};
         for (auto& L : ls) {
-            int w = 0;
-            for (int v = 1; v < jt_batch::WORKERS; ++v)
+            if (st == 0) {
+                L.free = true;
+                if (L.fused) {
+                    for (int i : L.slot_transform) L.free = L.free && b->plans[i]->d == 1;
+                } else {
+                    L.free = b->plans[L.transform]->d == 1;
+                }
+            }
+            const int w0 = L.free ? jt_batch::WORKERS : 0, w1 = L.free ? jt_batch::STREAMS : jt_batch::WORKERS;
+            int w = w0;
+            for (int v = w0 + 1; v < w1; ++v)
                 if (load[v] < load[w]) w = v;
             L.worker = w;
             load[w] += L.cost;
@@ -698,9 +713,15 @@ jt_status jt_batch_create(jt_batch** out, int count, jt_plan* const* plans, cons
         b->prec = prec;
         b->plans.assign(plans, plans + count);
         b->nrhs.assign(nrhs, nrhs + count);
-        for (int w = 0; w < jt_batch::WORKERS; ++w) {
-            if (cudaStreamCreateWithFlags(&b->work[w], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&b->ev_stage[w], cudaEventDisableTiming) != cudaSuccess ||
+        int prio_low = 0, prio_high = 0;
+        if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+            cudaGetLastError();
+            prio_high = prio_low = 0;
+        }
+        for (int w = 0; w < jt_batch::STREAMS; ++w) {
+            const int prio = (w < jt_batch::WORKERS) ? prio_low : prio_high;
+            if (cudaStreamCreateWithPriority(&b->work[w], cudaStreamNonBlocking, prio) != cudaSuccess ||
+                (w < jt_batch::WORKERS && cudaEventCreateWithFlags(&b->ev_stage[w], cudaEventDisableTiming) != cudaSuccess) ||
                 cudaEventCreateWithFlags(&b->ev_join[w], cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
                 jt_batch_destroy(b);
@@ -806,9 +827,9 @@ jt_status jt_batch_adjoint(jt_batch* batch, const void* const* in, void* const* 
 void jt_batch_destroy(jt_batch* batch) {
     if (!batch) return;
     if (batch->d_jobs) cudaFree(batch->d_jobs);
-    for (int w = 0; w < jt_batch::WORKERS; ++w) {
+    for (int w = 0; w < jt_batch::STREAMS; ++w) {
         if (batch->work[w]) cudaStreamDestroy(batch->work[w]);
-        if (batch->ev_stage[w]) cudaEventDestroy(batch->ev_stage[w]);
+        if (w < jt_batch::WORKERS && batch->ev_stage[w]) cudaEventDestroy(batch->ev_stage[w]);
         if (batch->ev_join[w]) cudaEventDestroy(batch->ev_join[w]);
     }
     if (batch->ev_fork) cudaEventDestroy(batch->ev_fork);
