@@ -642,6 +642,13 @@ def batch_full_mix(dev, stream, count=512):
             T.tune(m["nrhs"], stream=stream)
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t0
+        # the tuner's choices: how many sweeps (member x axis x direction) took each rank split
+        chosen = {}
+        for T, m in zip(Ts, members):
+            for ax in range(len(m["n"])):
+                for d in (0, 1):
+                    ks = T.schedule(ax, d, m["nrhs"])
+                    chosen[str(ks)] = chosen.get(str(ks), 0) + 1
         dt = torch.float32 if prec == "fp32" else torch.float64
         xs = [torch.tensor(host[i], dtype=dt, device=dev) for i in idx]
         fs = [torch.empty_like(x) for x in xs]
@@ -682,6 +689,7 @@ def batch_full_mix(dev, stream, count=512):
         ms_graph = e0.elapsed_time(e1) / reps
         out[prec] = {"members": len(members), "coeffs_per_step": coeffs, "eps": eps,
                      "plan_setup_many_s": setup_s, "tune_s": tune_s, "batch_create_s": batch_s,
+                     "tuned_rank_split_sweeps": chosen,
                      "batched": {"coeffs_per_s": coeffs / (ms_batch * 1e-3), "ms_per_step": ms_batch,
                                  "transforms_per_s": 2 * sum(m["nrhs"] for m in members) / (ms_batch * 1e-3)},
                      "graph_replay": {"coeffs_per_s": coeffs / (ms_graph * 1e-3), "ms_per_step": ms_graph,

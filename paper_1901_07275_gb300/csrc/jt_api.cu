@@ -172,10 +172,11 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
     std::vector<Cx<R>> ubtab, ovu, vown, fbtab;
     std::vector<int> bjtab, ovftab, ovj, bjf;
     int ovmode = 0, ovmax = 0, fbin = 0;
-    auto fill_ubtab = [&](int64_t TT) {
-        ubtab.assign((size_t)r * 18 * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
+    // u_k at the first two points of the bins m = t + TT s of slots s < nsl: [k][(s * 2 + i) * TT + t]
+    auto fill_ubtab = [&](int64_t TT, int64_t nsl) {
+        ubtab.assign((size_t)r * 2 * nsl * TT, Cx<R>{to_r(0.0, tag), to_r(0.0, tag)});
         for (int64_t k = 0; k < r; ++k)
-            for (int64_t s2 = 0; s2 <= 8; ++s2)
+            for (int64_t s2 = 0; s2 < nsl; ++s2)
                 for (int64_t t = 0; t < TT; ++t) {
                     const int64_t m = t + TT * s2;
                     if (m > L / 2) continue;
@@ -183,7 +184,7 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
                         const int64_t p = bin_ptr[m] + i;
                         if (p >= bin_ptr[m + 1]) break;
                         const int64_t j = bin_idx[p];
-                        ubtab[(size_t)k * 18 * TT + (s2 * 2 + i) * TT + t] = utab[(size_t)k * n + j];
+                        ubtab[(size_t)k * 2 * nsl * TT + (s2 * 2 + i) * TT + t] = utab[(size_t)k * n + j];
                     }
                 }
     };
@@ -257,7 +258,7 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
                 bjf.clear();
             }
         }
-        fill_ubtab(TT);
+        fill_ubtab(TT, 9);
     } else if (std::is_same<R, float>::value && ax.log2L > jt::F32_WARP_MAX_LOG2L) {
         // FP32 Stockham axes longer than 4096 (threads of T = L / 16, bins m = t + T e): the
         // adjoint's bin-ordered tables, and per thread a flag for a bin with more than two points
@@ -272,7 +273,24 @@ jt_status build_device_axis(DeviceAxis& ax, cudaStream_t s) {
                     if (bin_ptr[m] + i < bin_ptr[m + 1]) bjtab[(s2 * 2 + i) * TT + t] = bin_idx[bin_ptr[m] + i];
                 if (bin_ptr[m + 1] - bin_ptr[m] > 2) ovftab[2 * t] = 1;
             }
-        fill_ubtab(TT);
+        fill_ubtab(TT, 9);
+    } else if (std::is_same<R, dw>::value && ax.log2L <= jt::DW_SMEM_MAX_LOG2L) {
+        // Double-word Stockham axes (E = min(L, 8) elements a thread, TT = L / E threads, bins
+        // m = t + TT e): the adjoint's bin-ordered tables for the slots e < E / 2, so that
+        // u_k of one rank term takes L entries like v_k; bin L/2 (thread 0, slot E / 2) and the
+        // points past the first two of a bin are walked, on the threads flagged here
+        const int64_t E = std::min<int64_t>(L, 8), TT = L / E, nsl = E / 2;
+        bjtab.assign((size_t)2 * nsl * TT, -1);
+        ovftab.assign((size_t)2 * TT, 0);
+        for (int64_t s2 = 0; s2 < nsl; ++s2)
+            for (int64_t t = 0; t < TT; ++t) {
+                const int64_t m = t + TT * s2;
+                for (int i = 0; i < 2; ++i)
+                    if (bin_ptr[m] + i < bin_ptr[m + 1]) bjtab[(s2 * 2 + i) * TT + t] = bin_idx[bin_ptr[m] + i];
+                if (bin_ptr[m + 1] - bin_ptr[m] > 2) ovftab[2 * t] = 1;
+            }
+        if (bin_ptr[L / 2 + 1] > bin_ptr[L / 2]) ovftab[0] = 1;
+        fill_ubtab(TT, nsl);
     }
     AxisDev& A = ax.dev;
     A.n = (int)n;

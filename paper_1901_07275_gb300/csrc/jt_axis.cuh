@@ -364,13 +364,18 @@ struct Shape {
 // in pass order from the plan: at [NS - R0 + (r - 1) NS + k] the twiddle e^{2 pi i r k / (16 NS)}
 // of the pass of span NS, so that the 32 lanes of a pass read 32 consecutive entries (in
 // natural order they read one 32-byte sector each, and the table missed L1).
-// The FP32 long instances' adjoint gathers each bin's first two points from a bin-ordered copy
-// of u_k and a bin-ordered point table (AxisDev ubtab / bjtab, the layout of the four-step
-// kernel with T = L / 16) instead of walking the CSR lists: in the walk every bin's loads
-// waited on the previous bin's, one L2 round trip after another.
+// The adjoint of the FP32 long instances and of the double-word instances gathers each bin's
+// first two points from a bin-ordered copy of u_k and a bin-ordered point table (AxisDev ubtab
+// / bjtab, [k][(s * 2 + i) * T + t] for bin m = t + T s) instead of walking the CSR lists: in
+// the walk every bin's loads waited on the previous bin's (one L2 round trip after another in
+// FP32), and the trip counts differed from thread to thread; the double-word reads of u_k at
+// points two apart also met bank conflicts in the streamed slice.
 template <class R, int LOG2L>
 struct BinOrd {
-    static constexpr bool value = sizeof(R) == 4 && LOG2L >= 13;
+    static constexpr bool value = (sizeof(R) == 4 && LOG2L >= 13) || sizeof(R) == 8;
+    // bin slots of the table: FP32 the four-step kernel's nine (m = t + T s, s <= 8); double-
+    // word E / 2 (E = 8 elements a thread, or L when L < 8), bin L/2 then walked by thread 0
+    static constexpr int SLOTS = (sizeof(R) == 4) ? 9 : ((1 << LOG2L) < 8 ? (1 << LOG2L) : 8) / 2;
 };
 template <class R, int LOG2L>
 struct TwPass {
@@ -747,10 +752,11 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
         Cx<R>* dst = tsl + (i & 1) * (2 * L);
         unsigned long long* bar = tbar + (i & 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const unsigned vb = (unsigned)(sizeof(Cx<R>) * L), ub = (unsigned)(sizeof(Cx<R>) * n);
+        // forward: u_k in point order (n entries); adjoint: the bin-ordered copy (L entries)
+        const unsigned vb = (unsigned)(sizeof(Cx<R>) * L), ub = (unsigned)(sizeof(Cx<R>) * (FWD ? n : L));
         mbar_expect_tx(bar, vb + ub);
         bulk_g2s(dst, vtab + (size_t)k * L, vb, bar);
-        bulk_g2s(dst + L, utab + (size_t)k * n, ub, bar);
+        bulk_g2s(dst + L, FWD ? utab + (size_t)k * n : reinterpret_cast<const Cx<R>*>(A.ubtab) + (size_t)k * L, ub, bar);
     };
     // wait for this term's slice (bounded), then fetch the next; false if the wait ran out
     auto next_slice = [&](const Cx<R>*& vk, const Cx<R>*& uk) -> bool {
@@ -868,13 +874,14 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                 }
             }
             group_sync<T, G>(g);
-            // BinOrd: g at the first two points of each owned bin m = t + T e (e <= 8), from the
-            // bin-ordered point table (-1: none), held for the whole tile unless LEAN
+            // BinOrd: g at the first two points of each bin m = t + T e of the table's slots,
+            // from the bin-ordered point table (-1: none), held for the whole tile unless LEAN
             constexpr bool BINORD = BinOrd<R, LOG2L>::value;
-            R gb[(BINORD && !LEAN) ? 18 : 1];
+            constexpr int NSLT = BinOrd<R, LOG2L>::SLOTS;
+            R gb[(BINORD && !LEAN && NSLT > 0) ? 2 * NSLT : 1];
             if constexpr (BINORD && !LEAN) {
 #pragma unroll
-                for (int q = 0; q < 18; ++q) {
+                for (int q = 0; q < 2 * NSLT; ++q) {
                     const int j = __ldg(A.bjtab + q * T + t);
                     gb[q] = (j >= 0) ? aux[j] : RealOps<R>::zero();
                 }
@@ -887,13 +894,15 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                 Cx<R> x[E];
                 if constexpr (BINORD) {
                     // z[m] = u_k g at the bin's first two points (u_k in bin order, so that no
-                    // load waits on another), plus the rest of the bin from the CSR lists on
-                    // the lanes flagged as owning a bin with more than two points
-                    const Cx<R>* ubk = reinterpret_cast<const Cx<R>*>(A.ubtab) + (size_t)k * (18 * T);
+                    // load waits on another; streamed: the slice holds this table), plus, on the
+                    // threads flagged for it, the rest of the bin (and the bin L/2 when the table
+                    // has no slot for it) from the CSR lists
+                    const Cx<R>* ubk = STREAM ? uk : reinterpret_cast<const Cx<R>*>(A.ubtab) + (size_t)k * (2 * NSLT * T);
+                    const Cx<R>* ukg = utab + (size_t)k * n;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         Cx<R> z{RealOps<R>::zero(), RealOps<R>::zero()};
-                        if (e <= 8) {
+                        if (e < NSLT) {
                             const Cx<R> u0 = ubk[(2 * e) * T + t], u1 = ubk[(2 * e + 1) * T + t];
                             R g0, g1;
                             if constexpr (LEAN) {
@@ -904,16 +913,15 @@ __global__ void __launch_bounds__(Shape<R, LOG2L>::THREADS, (Shape<R, LOG2L>::TH
                                 g0 = gb[2 * e];
                                 g1 = gb[2 * e + 1];
                             }
-                            z.re = u0.re * g0 + u1.re * g1;
-                            z.im = u0.im * g0 + u1.im * g1;
-                            if (binx) {
-                                const int m = t + T * e;
-                                if (m <= L / 2) {
-                                    const int p2 = __ldg(bin_ptr + m + 1);
-                                    for (int p = __ldg(bin_ptr + m) + 2; p < p2; ++p) {
-                                        const int j = A.sorted ? p : __ldg(A.bin_idx + p);
-                                        z = bf_add(z, cscale(uk[j], aux[j]));
-                                    }
+                            z = bf_add(cscale(u0, g0), cscale(u1, g1));
+                        }
+                        if (binx) {
+                            const int m = t + T * e;
+                            if (m <= L / 2) {
+                                const int p2 = bin_ptr[m + 1];
+                                for (int p = bin_ptr[m] + (e < NSLT ? 2 : 0); p < p2; ++p) {
+                                    const int j = A.sorted ? p : __ldg(A.bin_idx + p);
+                                    z = bf_add(z, cscale(ukg[j], aux[j]));
                                 }
                             }
                         }
