@@ -71,6 +71,10 @@ struct GpuColumns;  // device copies of the tables the column walks read, made o
 GpuColumns* gpu_columns_create(const SetupRec& H, const AxisTables& T);  // nullptr on failure
 jt_status gpu_columns(GpuColumns* g, const std::vector<int>& cl, cd* out);
 void gpu_columns_destroy(GpuColumns* g);
+// The first k pivot columns of Householder QR with column pivoting of the m x n matrix A, held
+// row by row (A[i n + j]), on the GPU of that setup; the same steps and roundings as the host
+// routine la::qrcp_pivots (which takes the matrix column by column).
+jt_status gpu_qrcp_pivots(GpuColumns* g, const cd* A, int m, int n, int k, std::vector<int>& pivots);
 
 // Upper bound on the setup threads of the calling thread (jt_plan_create_many lowers it in
 // its workers so that plans set up side by side do not oversubscribe the host).

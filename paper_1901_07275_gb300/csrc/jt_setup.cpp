@@ -617,17 +617,31 @@ void randomized_svd(const AxisTables& T, const Entries& E, int r, int q, Sampler
         std::vector<int64_t> I64(I.begin(), I.end());
         std::vector<cd> rowsI((size_t)I.size() * N);
         E.rows(I64.data(), (int64_t)I.size(), rowsI.data());
-        std::vector<cd> A((size_t)I.size() * N);  // Z_{I,:}, |I| x N
-        for (size_t i = 0; i < I.size(); ++i)
-            for (int c = 0; c < N; ++c) A[i + (size_t)c * I.size()] = rowsI[i * (size_t)N + c];
-        Pcol = la::qrcp_pivots(std::move(A), (int)I.size(), N, std::min(r, (int)I.size()), g_setup_threads);
+        if (E.gpu) {
+            // on the GPU of the setup: Z_{I,:} as it comes, row by row
+            const jt_status st = gpu_qrcp_pivots(E.gpu, rowsI.data(), (int)I.size(), N, std::min(r, (int)I.size()), Pcol);
+            if (st != JT_OK) E.gpu_err = st;
+        } else {
+            std::vector<cd> A((size_t)I.size() * N);  // Z_{I,:}, |I| x N
+            for (size_t i = 0; i < I.size(); ++i)
+                for (int c = 0; c < N; ++c) A[i + (size_t)c * I.size()] = rowsI[i * (size_t)N + c];
+            Pcol = la::qrcp_pivots(std::move(A), (int)I.size(), N, std::min(r, (int)I.size()), g_setup_threads);
+        }
         J = unite(rng.pick(N, ncs, Pcol), Pcol);
         Cm.assign((size_t)n * J.size(), cd());
         E.cols(J, Cm.data());
-        std::vector<cd> Ch((size_t)J.size() * n);  // Z_{:,J}^H: pivoted LQ of Z_{:,J}
-        for (int j = 0; j < n; ++j)
-            for (size_t c = 0; c < J.size(); ++c) Ch[c + (size_t)j * J.size()] = std::conj(Cm[j + c * (size_t)n]);
-        Prow = la::qrcp_pivots(std::move(Ch), (int)J.size(), n, std::min(r, (int)J.size()), g_setup_threads);
+        // Z_{:,J}^H: pivoted LQ of Z_{:,J}
+        if (E.gpu) {
+            std::vector<cd> Chr((size_t)J.size() * n);  // row c: conj(Z_{:,J[c]})
+            for (size_t q = 0; q < Chr.size(); ++q) Chr[q] = std::conj(Cm[q]);
+            const jt_status st = gpu_qrcp_pivots(E.gpu, Chr.data(), (int)J.size(), n, std::min(r, (int)J.size()), Prow);
+            if (st != JT_OK) E.gpu_err = st;
+        } else {
+            std::vector<cd> Ch((size_t)J.size() * n);
+            for (int j = 0; j < n; ++j)
+                for (size_t c = 0; c < J.size(); ++c) Ch[c + (size_t)j * J.size()] = std::conj(Cm[j + c * (size_t)n]);
+            Prow = la::qrcp_pivots(std::move(Ch), (int)J.size(), n, std::min(r, (int)J.size()), g_setup_threads);
+        }
     }
     // step 5: orthonormal bases of Z_{:,Pcol} and Z_{Prow,:}^* (only the directions these
     // samples really have: kc <= |Pcol|, kr <= |Prow|)

@@ -4,8 +4,10 @@
 // host algorithms of jt_setup.cpp run with one thread per point: the three-term recurrence
 // of the orthonormal polynomials p_nu (and of the second-kind h_nu) walked in FP64, and in
 // double-word FP64 (pairs of doubles, Dekker 1971; Joldes, Muller, Popescu 2017) for points
-// with min(t, pi - t) < 0.35, where FP64 alone loses accuracy.  The small dense linear
-// algebra of the factorisation stays on the host.
+// with min(t, pi - t) < 0.35, where FP64 alone loses accuracy.  The column-pivoted QRs of
+// Algorithm 2.1 (steps 2-3, the pivots only) run here too, with the host routine's arithmetic
+// (jt_linalg.hpp qrcp_pivots); the orthonormal bases, the least-squares middle matrix and its
+// SVD (all of rank r or of r columns) stay on the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -244,6 +246,128 @@ __global__ void columns_kernel(Rec C, ColArgs A) {
 }
 
 // device buffers released on every path
+// ------------------------------------------------------------ pivoted QR (pivots only)
+// Businger--Golub Householder QR with column pivoting of an m x n complex matrix held row by
+// row (A[i n + j], so that the threads of a column-parallel update read consecutive words),
+// the first k steps, returning the pivot columns in order.  Every product and sum is rounded
+// on its own (no fused multiply-add) and each column's sums run over i in increasing order,
+// as in the host routine, so both pick the same pivots but for the last bits of |x0| (hypot).
+struct QrState {
+    double vn;   // squared norm of the current reflector; 0: no reflection this step
+    int stop;    // the pivot column was zero: every later step is skipped
+};
+__device__ __forceinline__ double qr_norm2(double2 z) { return __dadd_rn(__dmul_rn(z.x, z.x), __dmul_rn(z.y, z.y)); }
+
+__global__ void qr_norms_kernel(const double2* __restrict__ A, int m, int n, double* norms, int* perm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s = __dadd_rn(s, qr_norm2(A[(size_t)i * n + j]));
+    norms[j] = s;
+    perm[j] = j;
+}
+
+// Step s, one CTA: the largest remaining norm (first index on ties), the column swap, and
+// the reflector v (rows s..m-1) with its squared norm.
+constexpr int QR_PIVOT_THREADS = 1024;
+__global__ void __launch_bounds__(QR_PIVOT_THREADS) qr_pivot_kernel(double2* A, int m, int n, int s, double* norms,
+                                                                    int* perm, double2* v, QrState* st) {
+    __shared__ double bv[QR_PIVOT_THREADS];
+    __shared__ int bi[QR_PIVOT_THREADS];
+    __shared__ int piv;
+    if (st->stop) return;  // uniform: written by thread 0 of an earlier step
+    double best = -1.0;
+    int bidx = n;
+    for (int j = s + (int)threadIdx.x; j < n; j += QR_PIVOT_THREADS) {
+        const double x = norms[j];
+        if (x > best) {
+            best = x;
+            bidx = j;
+        }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int w = QR_PIVOT_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            const double o = bv[threadIdx.x + w];
+            const int oi = bi[threadIdx.x + w];
+            if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+                bv[threadIdx.x] = o;
+                bi[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) piv = (bv[0] > norms[s]) ? bi[0] : s;  // the host keeps s unless strictly larger
+    __syncthreads();
+    const int p = piv;
+    if (p != s) {
+        for (int i = threadIdx.x; i < m; i += QR_PIVOT_THREADS) {
+            const double2 a = A[(size_t)i * n + s];
+            A[(size_t)i * n + s] = A[(size_t)i * n + p];
+            A[(size_t)i * n + p] = a;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (p != s) {
+        const double t = norms[s];
+        norms[s] = norms[p];
+        norms[p] = t;
+        const int q = perm[s];
+        perm[s] = perm[p];
+        perm[p] = q;
+    }
+    double xn = 0.0;
+    for (int i = s; i < m; ++i) xn = __dadd_rn(xn, qr_norm2(A[(size_t)i * n + s]));
+    xn = sqrt(xn);
+    if (xn == 0.0) {
+        st->stop = 1;
+        st->vn = 0.0;
+        return;
+    }
+    const double2 x0 = A[(size_t)s * n + s];
+    const double ax0 = hypot(x0.x, x0.y);
+    const double2 ph = (ax0 > 0.0) ? make_double2(__ddiv_rn(x0.x, ax0), __ddiv_rn(x0.y, ax0)) : make_double2(1.0, 0.0);
+    const double2 alpha = make_double2(-__dmul_rn(ph.x, xn), -__dmul_rn(ph.y, xn));
+    double vn = 0.0;
+    for (int i = s; i < m; ++i) {
+        double2 vi = A[(size_t)i * n + s];
+        if (i == s) vi = make_double2(__dsub_rn(vi.x, alpha.x), __dsub_rn(vi.y, alpha.y));
+        v[i] = vi;
+        vn = __dadd_rn(vn, qr_norm2(vi));
+    }
+    st->vn = vn;
+}
+
+// Step s: reflect every column j > s (one thread a column) and recompute its trailing norm.
+__global__ void qr_update_kernel(double2* A, int m, int n, int s, double* norms, const double2* __restrict__ v,
+                                 const QrState* st) {
+    const int j = s + 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || st->stop || st->vn == 0.0) return;
+    double2 w = make_double2(0.0, 0.0);
+    for (int i = s; i < m; ++i) {
+        const double2 vi = v[i], c = A[(size_t)i * n + j];
+        // conj(v_i) c_i
+        w.x = __dadd_rn(w.x, __dsub_rn(__dmul_rn(vi.x, c.x), __dmul_rn(-vi.y, c.y)));
+        w.y = __dadd_rn(w.y, __dadd_rn(__dmul_rn(vi.x, c.y), __dmul_rn(-vi.y, c.x)));
+    }
+    const double f = __ddiv_rn(2.0, st->vn);
+    w = make_double2(__dmul_rn(w.x, f), __dmul_rn(w.y, f));
+    double nn = 0.0;
+    for (int i = s; i < m; ++i) {
+        const double2 vi = v[i];
+        double2 c = A[(size_t)i * n + j];
+        const double2 wv = make_double2(__dsub_rn(__dmul_rn(w.x, vi.x), __dmul_rn(w.y, vi.y)),
+                                        __dadd_rn(__dmul_rn(w.x, vi.y), __dmul_rn(w.y, vi.x)));
+        c = make_double2(__dsub_rn(c.x, wv.x), __dsub_rn(c.y, wv.y));
+        A[(size_t)i * n + j] = c;
+        if (i > s) nn = __dadd_rn(nn, qr_norm2(c));
+    }
+    norms[j] = nn;
+}
+
 struct DevBufs {
     std::vector<void*> p;
     ~DevBufs() {
@@ -316,8 +440,23 @@ struct GpuColumns {
     size_t out_cap = 0;
     std::vector<int> hslot;
     cudaStream_t stream = nullptr;
+    // pivoted-QR work area (grown as needed): the matrix, its column norms, the permutation,
+    // the reflector and the step state
+    double2* qa = nullptr;
+    size_t qa_cap = 0;
+    double* qnorm = nullptr;
+    int* qperm = nullptr;
+    size_t qn_cap = 0;
+    double2* qv = nullptr;
+    int qv_cap = 0;
+    QrState* qst = nullptr;
     ~GpuColumns() {
         if (out) cudaFree(out);
+        if (qa) cudaFree(qa);
+        if (qnorm) cudaFree(qnorm);
+        if (qperm) cudaFree(qperm);
+        if (qv) cudaFree(qv);
+        if (qst) cudaFree(qst);
         if (stream) cudaStreamDestroy(stream);
     }
 };
@@ -389,6 +528,67 @@ jt_status gpu_columns(GpuColumns* g, const std::vector<int>& cl, cd* out) {
         cudaMemcpyAsync(out, g->out, sizeof(double2) * need, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
         cudaStreamSynchronize(g->stream) != cudaSuccess) {
         cudaGetLastError();
+        return JT_ECUDA;
+    }
+    return JT_OK;
+}
+
+
+jt_status gpu_qrcp_pivots(GpuColumns* g, const cd* A, int m, int n, int k, std::vector<int>& pivots) {
+    pivots.clear();
+    if (!g) return JT_ECUDA;
+    k = std::min(k, std::min(m, n));
+    if (k <= 0) return JT_OK;
+    const size_t need = (size_t)m * (size_t)n;
+    auto grow = [](auto*& p, auto& cap, size_t count) -> bool {
+        if ((size_t)count <= (size_t)cap) return true;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMalloc((void**)&p, sizeof(*p) * count) != cudaSuccess) return false;
+        cap = count;
+        return true;
+    };
+    bool ok = grow(g->qa, g->qa_cap, need);
+    if (ok && (size_t)n > g->qn_cap) {
+        if (g->qnorm) cudaFree(g->qnorm);
+        if (g->qperm) cudaFree(g->qperm);
+        g->qnorm = nullptr;
+        g->qperm = nullptr;
+        g->qn_cap = 0;
+        ok = cudaMalloc((void**)&g->qnorm, sizeof(double) * n) == cudaSuccess &&
+             cudaMalloc((void**)&g->qperm, sizeof(int) * n) == cudaSuccess;
+        if (ok) g->qn_cap = (size_t)n;
+    }
+    ok = ok && grow(g->qv, g->qv_cap, (size_t)m);
+    if (ok && !g->qst) ok = cudaMalloc((void**)&g->qst, sizeof(QrState)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return JT_ECUDA;
+    }
+    static_assert(sizeof(cd) == sizeof(double2), "complex<double> and double2 share a layout");
+    cudaStream_t s = g->stream;
+    const QrState st0{0.0, 0};
+    if (cudaMemcpyAsync(g->qa, A, sizeof(double2) * need, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(g->qst, &st0, sizeof(QrState), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return JT_ECUDA;
+    }
+    const int threads = 128;
+    qr_norms_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(g->qa, m, n, g->qnorm, g->qperm);
+    for (int step = 0; step < k; ++step) {
+        qr_pivot_kernel<<<1, QR_PIVOT_THREADS, 0, s>>>(g->qa, m, n, step, g->qnorm, g->qperm, g->qv, g->qst);
+        const int rest = n - (step + 1);
+        if (rest > 0)
+            qr_update_kernel<<<(unsigned)((rest + threads - 1) / threads), threads, 0, s>>>(g->qa, m, n, step, g->qnorm,
+                                                                                         g->qv, g->qst);
+    }
+    pivots.assign((size_t)k, 0);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(pivots.data(), g->qperm, sizeof(int) * k, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        pivots.clear();
         return JT_ECUDA;
     }
     return JT_OK;
