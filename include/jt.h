@@ -79,9 +79,10 @@ typedef struct {
                                (as jt_plan_tune does) before building the batch */
     int32_t kind;           /* JT_FIRST_KIND (default) or JT_SECOND_KIND */
     int32_t setup_device;   /* 0 (default): the whole setup on the host; 1: the Newton iteration
-                               for the nodes and the sampled columns of B (the O(n^2) steps) in
-                               FP64 kernels on the current GPU, the rest on the host.  Same
-                               algorithm; tables agree with the host's to rounding. */
+                               for the nodes, the sampled columns of B (the O(n^2) steps) and
+                               the column-pivoted QRs of Algorithm 2.1 in FP64 kernels on the
+                               current GPU, the rest on the host.  Same algorithm; tables agree
+                               with the host's to rounding. */
 } jt_options;
 
 /* Which modified Jacobi functions the transform expands in (Sec. 1, Eqs. eq:jacnonosci,
